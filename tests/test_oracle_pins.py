@@ -1,0 +1,533 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the mathematics:
+closed forms, invariants, special cases and brute force on tiny inputs.
+
+None of these tests re-types an oracle formula: each checks the oracle through a
+different route (symbolic integration, dense linear algebra, a sequential algorithm
+proven equivalent to the parallel one, convergence rates of the PDE solution).
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from paper_1204_2586_gb300.inputs import kappa_lognormal, kuhn_mesh, splitmix64
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")
+
+
+def _mesh(n, seed=0):
+    return kuhn_mesh(n, 0.2, seed)
+
+
+# ---------------------------------------------------------------------------------
+# Quadrature (load vector of Eq. 7): Grundmann-Moeller exactness on monomials
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("s", [0, 1, 2, 3, 4, 5])
+def test_gm_rule_exact_to_degree(oracle_mod, s):
+    lam, w = oracle_mod.gm_rule(s)
+    assert np.isclose(w.sum(), 1.0 / 6.0, rtol=0, atol=1e-14)
+    d = 2 * s + 1
+    for deg in range(d + 1):
+        for a in itertools.product(range(deg + 1), repeat=4):
+            if sum(a) != deg:
+                continue
+            exact = math.prod(math.factorial(x) for x in a) / math.factorial(deg + 3)
+            got = np.sum(w * np.prod(lam ** np.array(a), axis=1))
+            assert abs(got - exact) <= 1e-13 * max(1.0, exact) + 1e-16, (s, a)
+    # and the degree claim is sharp for s >= 1: some monomial of degree d+1 is missed
+    if s >= 1:
+        a = (d + 1, 0, 0, 0)
+        exact = math.factorial(d + 1) / math.factorial(d + 4)
+        got = np.sum(w * lam[:, 0] ** (d + 1))
+        assert abs(got - exact) > 1e-12 * exact
+
+
+# ---------------------------------------------------------------------------------
+# P_k basis (Sec. 2): nodal (Kronecker) property and partition of unity
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_basis_nodal_and_partition(oracle_mod, k):
+    nodes = oracle_mod.ref_nodes(k)
+    assert nodes.shape[0] == (k + 1) * (k + 2) * (k + 3) // 6
+    assert np.all(nodes.sum(1) == k)
+    for n, m in enumerate(nodes):
+        phi = oracle_mod.basis_eval(k, m / k)
+        e = np.zeros(len(nodes))
+        e[n] = 1
+        assert np.allclose(phi, e, atol=1e-13)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        lam = rng.dirichlet(np.ones(4))
+        assert abs(oracle_mod.basis_eval(k, lam).sum() - 1.0) < 1e-13
+
+
+# ---------------------------------------------------------------------------------
+# Element stiffness (Eq. 7) against an independent symbolic computation: Cartesian
+# monomial basis from the Vandermonde matrix on the reference tetrahedron, exact
+# integrals by sympy, affine map to a random physical tetrahedron.
+# ---------------------------------------------------------------------------------
+def _sympy_stiffness(k, X, nodes):
+    sympy = pytest.importorskip("sympy")
+    x, y, z = sympy.symbols("x y z")
+    monos = [x ** a * y ** b * z ** c for a in range(k + 1) for b in range(k + 1 - a)
+             for c in range(k + 1 - a - b)]
+    vhat = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    pts = [tuple(sympy.Rational(sum(int(m[a]) * vhat[a][c] for a in range(4)), k)
+                 for c in range(3)) for m in nodes]
+    V = sympy.Matrix([[mo.subs({x: p[0], y: p[1], z: p[2]}) for mo in monos] for p in pts])
+    Cm = V.inv()  # phi_n = sum_c Cm[c, n] mono_c
+    basis = [sum(Cm[c, n] * monos[c] for c in range(len(monos))) for n in range(len(pts))]
+    grads = [[sympy.diff(b, v) for v in (x, y, z)] for b in basis]
+    J = np.array([X[1] - X[0], X[2] - X[0], X[3] - X[0]]).T
+    Jit = np.linalg.inv(J).T
+    det = np.linalg.det(J)
+    cache = {}
+
+    def integ(expr):
+        expr = sympy.expand(expr)
+        if expr == 0:
+            return 0.0
+        key = sympy.srepr(expr)
+        if key not in cache:
+            cache[key] = float(sympy.integrate(expr, (z, 0, 1 - x - y), (y, 0, 1 - x), (x, 0, 1)))
+        return cache[key]
+
+    n = len(basis)
+    # M[p,q][m,n] = int dphi_m/dxi_p dphi_n/dxi_q over the reference tet
+    M = np.zeros((3, 3, n, n))
+    for p in range(3):
+        for q in range(3):
+            for a in range(n):
+                for b in range(a, n):
+                    v = integ(grads[a][p] * grads[b][q])
+                    M[p, q, a, b] = v
+                    M[q, p, b, a] = v
+    K = np.zeros((n, n))
+    G = Jit.T @ Jit  # grad_x phi = J^{-T} grad_xi phi
+    for p in range(3):
+        for q in range(3):
+            K += G[p, q] * M[p, q]
+    return K * det
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_element_stiffness_vs_symbolic(oracle_mod, k):
+    rng = np.random.default_rng(k)
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float) + 0.2 * rng.standard_normal((4, 3))
+    if np.linalg.det(np.array([X[1] - X[0], X[2] - X[0], X[3] - X[0]]).T) < 0:
+        X[[2, 3]] = X[[3, 2]]
+    K = oracle_mod.element_stiffness(k, X, 1.7)
+    Ks = 1.7 * _sympy_stiffness(k, X, oracle_mod.ref_nodes(k))
+    assert np.allclose(K, Ks, rtol=1e-12, atol=1e-12 * np.abs(Ks).max())
+
+
+# ---------------------------------------------------------------------------------
+# Assembled operators (Sec. 2)
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_neumann_matrix_zero_row_sums_and_symmetry(oracle_mod, k):
+    xyz, t = _mesh(3)
+    kap = kappa_lognormal(t.shape[0], 1)
+    P = oracle_mod.Problem(xyz, t, k, kap, dirichlet=False)
+    A = P.matrix(0).to_scipy()
+    assert P.nh == P.nall
+    rs = np.abs(A @ np.ones(P.nh))
+    assert rs.max() <= 1e-12 * abs(A).max()
+    assert abs(A - A.T).max() <= 1e-13 * abs(A).max()
+    AH = P.matrix(1).to_scipy()
+    assert (np.abs(AH @ np.ones(P.nH))).max() <= 1e-12 * abs(AH).max()
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_dirichlet_matrix_spd(oracle_mod, k):
+    xyz, t = _mesh(2)
+    P = oracle_mod.Problem(xyz, t, k)
+    A = P.matrix(0).to_scipy().toarray()
+    assert np.allclose(A, A.T, atol=1e-14 * np.abs(A).max())
+    np.linalg.cholesky(A)  # raises if not positive definite
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_galerkin_identity(oracle_mod, k):
+    """A_H = I_R A_h I_P (Sec. 2, after Eq. 10) with element-wise kappa."""
+    xyz, t = _mesh(3)
+    kap = kappa_lognormal(t.shape[0], 1)
+    for dirichlet in (True, False):
+        P = oracle_mod.Problem(xyz, t, k, kap, dirichlet=dirichlet)
+        A = P.matrix(0).to_scipy()
+        AH = P.matrix(1).to_scipy()
+        Pi = P.matrix(2).to_scipy()
+        G = (Pi.T @ A @ Pi).toarray()
+        assert np.abs(G - AH.toarray()).max() <= 1e-13 * np.abs(AH).max()
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_pi_reproduces_affine_functions(oracle_mod, k):
+    """c_j^i = psi_j(x_i^h) (Eq. 10): I_P maps P1 nodal values of an affine function to
+    its P_k nodal values, exactly, on the full space."""
+    xyz, t = _mesh(3)
+    P = oracle_mod.Problem(xyz, t, k, dirichlet=False)
+    Pi = P.matrix(2).to_scipy()
+    _, dx = P.dofs()
+    assert np.allclose(Pi @ np.ones(P.nH), 1.0, atol=1e-14)
+    for coef in ([1.0, -2.0, 0.5, 3.0], [0.0, 1.0, 1.0, 1.0]):
+        g = lambda X: coef[0] + X @ np.array(coef[1:])  # noqa: E731
+        assert np.allclose(Pi @ g(xyz), g(dx), atol=1e-13)
+    vals = Pi.data
+    assert np.all(np.isin(np.round(vals * k), np.arange(1, k + 1)))
+    assert np.allclose(vals * k, np.round(vals * k), atol=1e-15)
+
+
+def test_kuhn_sizes_match_closed_form(oracle_mod):
+    """Interior DOF count of P_k on n^3 Kuhn cubes is (kn-1)^3; P1 count (n-1)^3."""
+    for k, n in [(2, 4), (3, 3), (4, 2)]:
+        xyz, t = _mesh(n)
+        P = oracle_mod.Problem(xyz, t, k)
+        assert P.nh == (k * n - 1) ** 3
+        assert P.nH == (n - 1) ** 3
+        assert P.nall == (k * n + 1) ** 3
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_manufactured_solution_rate(oracle_mod, k):
+    """u = sin(pi x) sin(pi y) sin(pi z): the L2 error of the P_k solution converges at
+    O(h^{k+1}); measured between n = 4 and n = 8 on jittered meshes."""
+    errs = []
+    for n in (4, 8):
+        xyz, t = _mesh(n)
+        P = oracle_mod.Problem(xyz, t, k)
+        A = P.matrix(0).to_scipy().tocsc()
+        u = spla.spsolve(A, P.rhs())
+        errs.append(P.l2_error_sine(u))
+    rate = math.log2(errs[0] / errs[1])
+    assert rate >= k + 0.8, (errs, rate)
+
+
+# ---------------------------------------------------------------------------------
+# Colouring: Jones-Plassmann with fixed priorities equals the sequential greedy
+# colouring in decreasing priority order.
+# ---------------------------------------------------------------------------------
+def _greedy_colouring(A, stream):
+    n = A.shape[0]
+    h = splitmix64(stream, np.arange(n))
+    order = sorted(range(n), key=lambda i: (-int(h[i]), i))
+    col = -np.ones(n, int)
+    for i in order:
+        nb = A.indices[A.indptr[i]:A.indptr[i + 1]]
+        used = {col[j] for j in nb if j != i and col[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        col[i] = c
+    return col
+
+
+@pytest.mark.parametrize("k,n", [(2, 3), (3, 2), (1, 5)])
+def test_colouring_equals_sequential_greedy(oracle_mod, k, n):
+    xyz, t = _mesh(n)
+    P = oracle_mod.Problem(xyz, t, max(k, 2))
+    A = P.matrix(0 if k > 1 else 1)
+    stream = oracle_mod.stream_colour(7, 0)
+    c, nc = oracle_mod.colour_jp(A, stream)
+    S = A.to_scipy()
+    assert np.array_equal(c, _greedy_colouring(S, stream))
+    assert nc == c.max() + 1
+    r, cc = S.nonzero()
+    off = r != cc
+    assert np.all(c[r[off]] != c[cc[off]])
+
+
+# ---------------------------------------------------------------------------------
+# Smoothers
+# ---------------------------------------------------------------------------------
+def test_sgs_closed_form(oracle_mod):
+    """One forward plus one backward multicolour GS sweep from zero is
+    (D+U)^{-1} D (D+L)^{-1} r in the colour-sorted ordering; it is symmetric."""
+    xyz, t = _mesh(2)
+    P = oracle_mod.Problem(xyz, t, 3, kappa_lognormal(t.shape[0], 1))
+    A = P.matrix(0)
+    c, nc = oracle_mod.colour_jp(A, 123)
+    perm = np.lexsort((np.arange(len(c)), c))
+    Ad = A.to_scipy().toarray()[np.ix_(perm, perm)]
+    D = np.diag(np.diag(Ad))
+    Lo = np.tril(Ad, -1)
+    Up = np.triu(Ad, 1)
+    rng = np.random.default_rng(0)
+    r = rng.standard_normal(P.nh)
+    y = sla.solve_triangular(D + Lo, r[perm], lower=True)
+    zp = sla.solve_triangular(D + Up, D @ y, lower=False)
+    z = oracle_mod.sgs(A, c, nc, r)
+    assert np.allclose(z[perm], zp, rtol=1e-12, atol=1e-12 * np.abs(zp).max())
+    s = rng.standard_normal(P.nh)
+    zs = oracle_mod.sgs(A, c, nc, s)
+    assert abs(s @ z - r @ zs) <= 1e-12 * abs(s @ z)
+
+
+def test_l1_jacobi_closed_form(oracle_mod):
+    xyz, t = _mesh(2)
+    P = oracle_mod.Problem(xyz, t, 2)
+    P.setup(smoother=1)
+    A = P.matrix(0).to_scipy()
+    r = np.random.default_rng(1).standard_normal(P.nh)
+    d = np.asarray(abs(A).sum(axis=1)).ravel()
+    assert np.allclose(P.smoother(r), r / d, rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------------
+# AMG pieces
+# ---------------------------------------------------------------------------------
+def _p1_matrix(oracle_mod, n=6, dirichlet=True, seed=0):
+    xyz, t = kuhn_mesh(n, 0.2, seed)
+    P = oracle_mod.Problem(xyz, t, 2, kappa_lognormal(t.shape[0], 1), dirichlet=dirichlet)
+    return P.matrix(1)
+
+
+def test_strength_definition(oracle_mod):
+    """Sec. 6.2: j strong for i iff -a_ij > theta max_{k != i}(-a_ik)."""
+    A = _p1_matrix(oracle_mod)
+    for theta in (0.25, 0.5, 0.8):
+        s = oracle_mod.strength(A, theta)
+        S = A.to_scipy()
+        for i in range(S.shape[0]):
+            lo, hi = S.indptr[i], S.indptr[i + 1]
+            cols, vals = S.indices[lo:hi], S.data[lo:hi]
+            off = cols != i
+            mx = (-vals[off]).max()
+            want = off & (-vals > theta * mx) if mx > 0 else np.zeros_like(off)
+            assert np.array_equal(s[lo:hi].astype(bool), want)
+
+
+def _sequential_pmis(S, strong, stream):
+    """PMIS with fixed measures equals this sequential rule: visit points in decreasing
+    (|S_i^T|, hash, i); an undecided point becomes C and every undecided point that
+    strongly depends on it becomes F."""
+    n = S.shape[0]
+    Sg = sp.csr_matrix((strong.astype(float), S.indices.copy(), S.indptr.copy()), shape=S.shape)
+    Sg.eliminate_zeros()
+    mu = np.asarray((Sg != 0).sum(axis=0)).ravel()
+    deg = np.diff(Sg.indptr)
+    h = splitmix64(stream, np.arange(n))
+    cf = np.zeros(n, int)
+    cf[(deg == 0) & (mu == 0)] = -1
+    ST = Sg.T.tocsr()
+    order = sorted(range(n), key=lambda i: (-int(mu[i]), -int(h[i]), -i))
+    for i in order:
+        if cf[i] != 0:
+            continue
+        cf[i] = 1
+        for j in ST.indices[ST.indptr[i]:ST.indptr[i + 1]]:  # j depends on i
+            if cf[j] == 0:
+                cf[j] = -1
+    return cf
+
+
+@pytest.mark.parametrize("theta", [0.25, 0.6])
+def test_pmis_equals_sequential_rule(oracle_mod, theta):
+    A = _p1_matrix(oracle_mod, 7)
+    s = oracle_mod.strength(A, theta)
+    stream = oracle_mod.stream_pmis(3, 0)
+    cf = oracle_mod.pmis(A, s, stream)
+    assert np.array_equal(cf, _sequential_pmis(A.to_scipy(), s, stream))
+    # validity: every F point with a strong dependency depends on some C point unless
+    # it was isolated; no two C points depend strongly on each other
+    S = A.to_scipy()
+    rows = np.repeat(np.arange(S.shape[0]), np.diff(S.indptr))
+    st = s.astype(bool)
+    for i in np.nonzero(cf == -1)[0]:
+        dep = S.indices[S.indptr[i]:S.indptr[i + 1]][st[S.indptr[i]:S.indptr[i + 1]]]
+        if dep.size:
+            assert np.any(cf[dep] == 1)
+    pairs = set(zip(rows[st], S.indices[st]))
+    for (i, j) in pairs:
+        if cf[i] == 1 and cf[j] == 1:
+            assert (j, i) not in pairs
+
+
+def test_extpi_preserves_constants_and_pattern(oracle_mod):
+    """On a zero-row-sum matrix extended+i interpolation reproduces constants exactly,
+    and row i's columns are C_i^s plus the strong C points of F_i^s."""
+    A = _p1_matrix(oracle_mod, 6, dirichlet=False)
+    s = oracle_mod.strength(A, 0.25)
+    cf = oracle_mod.pmis(A, s, 11)
+    Pm = oracle_mod.extpi(A, s, cf)
+    Ps = Pm.to_scipy()
+    nc = int((cf == 1).sum())
+    assert Ps.shape == (A.shape[0], nc)
+    rs = np.asarray(Ps.sum(axis=1)).ravel()
+    has = np.diff(Ps.indptr) > 0
+    assert np.allclose(rs[has], 1.0, atol=1e-12)
+    S = A.to_scipy()
+    Sb = sp.csr_matrix((s.astype(float), S.indices.copy(), S.indptr.copy()), shape=S.shape)
+    Sb.eliminate_zeros()
+    Cm = sp.diags((cf == 1).astype(float))
+    Fm = sp.diags((cf == -1).astype(float))
+    reach = (Sb @ Cm + Sb @ Fm @ Sb @ Cm).tocsr()
+    cidx = np.cumsum(cf == 1) - 1
+    for i in np.nonzero(cf == -1)[0]:
+        want = sorted(set(cidx[reach.indices[reach.indptr[i]:reach.indptr[i + 1]]]))
+        got = list(Ps.indices[Ps.indptr[i]:Ps.indptr[i + 1]])
+        assert got == want
+    for i in np.nonzero(cf == 1)[0]:
+        assert list(Ps.indices[Ps.indptr[i]:Ps.indptr[i + 1]]) == [cidx[i]]
+        assert Ps.data[Ps.indptr[i]] == 1.0
+
+
+def test_rap_matches_dense_product(oracle_mod):
+    A = _p1_matrix(oracle_mod, 6)
+    s = oracle_mod.strength(A, 0.25)
+    cf = oracle_mod.pmis(A, s, 5)
+    Pm = oracle_mod.extpi(A, s, cf)
+    Ac = oracle_mod.rap(A, Pm)
+    D = Pm.to_scipy().toarray()
+    want = D.T @ A.to_scipy().toarray() @ D
+    got = Ac.to_scipy().toarray()
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+    # structural pattern: every product term appears
+    pat = (abs(Pm.to_scipy()).T @ abs(A.to_scipy()) @ abs(Pm.to_scipy())).tocsr()
+    assert np.array_equal(pat.indptr, Ac.ptr)
+
+
+# ---------------------------------------------------------------------------------
+# Preconditioner and solver
+# ---------------------------------------------------------------------------------
+def _dense_ops(P):
+    A = P.matrix(0).to_scipy().toarray()
+    Pi = P.matrix(2).to_scipy().toarray()
+    AH = P.matrix(1).to_scipy().toarray()
+    return A, Pi, AH
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_two_level_closed_form(oracle_mod, mode):
+    """With the exact coarse solve (one AMG level), the additive preconditioner is
+    S_sgs + I_P A_H^{-1} I_R, and the multiplicative one (Algorithm 2.1 with
+    pre-smoothing) has error operator (I - S_b A)(I - I_P A_H^{-1} I_R A)(I - S_f A)."""
+    xyz, t = _mesh(3)
+    P = oracle_mod.Problem(xyz, t, 2, kappa_lognormal(t.shape[0], 1))
+    P.setup(mode=mode, coarse_size=10 ** 6)
+    assert P.levels() == 1
+    A, Pi, AH = _dense_ops(P)
+    c = P.fine_colour()
+    perm = np.lexsort((np.arange(len(c)), c))
+    inv = np.argsort(perm)
+    Ap = A[np.ix_(perm, perm)]
+    D = np.diag(np.diag(Ap))
+    Sf = np.linalg.inv(D + np.tril(Ap, -1))[np.ix_(inv, inv)]
+    Sb = np.linalg.inv(D + np.triu(Ap, 1))[np.ix_(inv, inv)]
+    Cc = Pi @ np.linalg.solve(AH, Pi.T)
+    n = A.shape[0]
+    I = np.eye(n)
+    Bm = np.column_stack([P.apply_prec(I[:, j]) for j in range(n)])
+    if mode == 0:
+        want = Sb @ D[np.ix_(inv, inv)] @ Sf + Cc
+        assert np.abs(Bm - want).max() <= 1e-11 * np.abs(want).max()
+    else:
+        E = (I - Sb @ A) @ (I - Cc @ A) @ (I - Sf @ A)
+        assert np.abs((I - Bm @ A) - E).max() <= 1e-11
+    assert np.abs(Bm - Bm.T).max() <= 1e-11 * np.abs(Bm).max()
+    assert np.linalg.eigvalsh(0.5 * (Bm + Bm.T)).min() > 0
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("lsm", [0, 1])
+def test_multilevel_preconditioner_symmetric_positive(oracle_mod, mode, lsm):
+    xyz, t = _mesh(5)
+    P = oracle_mod.Problem(xyz, t, 2, kappa_lognormal(t.shape[0], 1))
+    P.setup(mode=mode, level_smoother=lsm, coarse_size=8)
+    assert P.levels() >= 2
+    rng = np.random.default_rng(2)
+    x, y = rng.standard_normal(P.nh), rng.standard_normal(P.nh)
+    bx, by = P.apply_prec(x), P.apply_prec(y)
+    assert abs(y @ bx - x @ by) <= 1e-12 * abs(y @ bx)
+    assert x @ bx > 0
+    # the V-cycle on its own is symmetric too
+    u, v = rng.standard_normal(P.nH), rng.standard_normal(P.nH)
+    assert abs(v @ P.vcycle(u) - u @ P.vcycle(v)) <= 1e-12 * abs(v @ P.vcycle(u))
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_pcg_reaches_dense_solution(oracle_mod, k):
+    xyz, t = _mesh(2)
+    P = oracle_mod.Problem(xyz, t, k, kappa_lognormal(t.shape[0], 1))
+    P.setup(tol=1e-13)
+    out = P.solve()
+    assert out["status"] == 0
+    A = P.matrix(0).to_scipy().toarray()
+    u = np.linalg.solve(A, P.rhs())
+    assert np.linalg.norm(out["x"] - u) <= 1e-10 * np.linalg.norm(u)
+    assert out["true_rel"] <= 1e-13 * 1.01
+
+
+def test_fcg_matches_pcg_with_fixed_preconditioner(oracle_mod):
+    """With a fixed SPD preconditioner the flexible beta equals the standard one in exact
+    arithmetic, so the two iterations coincide up to rounding."""
+    xyz, t = _mesh(4)
+    P = oracle_mod.Problem(xyz, t, 3)
+    P.setup(flexible=0)
+    a = P.solve()
+    P.setup(flexible=1)
+    b = P.solve()
+    assert a["iters"] == b["iters"]
+    assert np.allclose(a["hist"], b["hist"], rtol=1e-6)
+
+
+@pytest.mark.slow
+def test_iterations_independent_of_h(oracle_mod):
+    """Theorem 4.2: the two-level convergence rate is bounded independently of h."""
+    its = {}
+    for mode in (0, 1):
+        for n in (4, 8, 16):
+            xyz, t = _mesh(n)
+            P = oracle_mod.Problem(xyz, t, 2)
+            P.setup(mode=mode)
+            out = P.solve()
+            assert out["status"] == 0
+            its[(mode, n)] = out["iters"]
+        vals = [its[(mode, n)] for n in (4, 8, 16)]
+        assert max(vals) - min(vals) <= 4, its
+
+
+def test_theta_robustness(oracle_mod):
+    """Tables 2-4: the auxiliary-space method is nearly insensitive to theta."""
+    xyz, t = _mesh(6)
+    P = oracle_mod.Problem(xyz, t, 3)
+    its = []
+    for theta in (0.2, 0.4, 0.6, 0.8):
+        P.setup(theta=theta, mode=1)
+        out = P.solve()
+        assert out["status"] == 0
+        its.append(out["iters"])
+    assert max(its) - min(its) <= 3, its
+
+
+def test_adjoint_gradient_matches_central_differences(oracle_mod):
+    """dL/dkappa_e = -lambda_e^T Khat_e u_e with A lambda = u - u_obs, against central
+    differences of L = 0.5 ||u - u_obs||^2 computed with direct solves."""
+    xyz, t = _mesh(2)
+    kap = kappa_lognormal(t.shape[0], 1)
+    kobs = kappa_lognormal(t.shape[0], 3)
+    P = oracle_mod.Problem(xyz, t, 2, kap)
+    Q = oracle_mod.Problem(xyz, t, 2, kobs)
+    uobs = spla.spsolve(Q.matrix(0).to_scipy().tocsc(), Q.rhs())
+
+    def loss(kv):
+        P.set_kappa(kv)
+        u = spla.spsolve(P.matrix(0).to_scipy().tocsc(), P.rhs())
+        return 0.5 * np.sum((u - uobs) ** 2), u
+
+    L0, u = loss(kap)
+    A = P.matrix(0).to_scipy().tocsc()
+    lam = spla.spsolve(A, u - uobs)
+    g = P.grad_kappa(u, lam)
+    eps = 1e-6
+    for e in [0, 5, 17, 40]:
+        kp, km = kap.copy(), kap.copy()
+        kp[e] += eps
+        km[e] -= eps
+        fd = (loss(kp)[0] - loss(km)[0]) / (2 * eps)
+        assert abs(fd - g[e]) <= 1e-6 * max(abs(g).max(), 1e-30), (e, fd, g[e])
