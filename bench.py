@@ -1,0 +1,290 @@
+"""Benchmark: auxiliary-space PCG to relative residual 1e-8 on the P3 Poisson problem of a
+32^3-cube jittered Kuhn mesh (196,608 tetrahedra, 857,375 unknowns), kappa = 1, sine
+source, additive preconditioner (one symmetric multicolour GS sweep + one P1 AMG
+V(1,1)-cycle, PMIS + extended+i, theta = 0.25), FP64 throughout.
+
+One step = one complete PCG solve from x0 = 0 (setup excluded, reported separately).
+The metric is MDOF*iter/s = n_h * iterations / solve time; the time to solution and the
+HBM roofline of the dominant kernel are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: the path runs as independent replicas (one solve per rank, no collective on
+the data path); value sums the ranks' work over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="p3_n32", k=3, n=32, jitter=0.2, mesh_seed=0)
+METRIC = "P_k PCG time to rel. residual 1e-8 (s), MDOF*iter/s, HBM GB/s vs peak"
+UNIT = "MDOF*iter/s"
+CONFIG = {
+    "workload": "P3 Poisson, kappa=1, 32^3 jittered Kuhn cubes (196,608 tets, 857,375 unknowns), "
+                "sine source, FP64, PCG to rel. residual 1e-8, additive aux-space preconditioner "
+                "(1 SGS sweep + 1 P1 AMG V-cycle, PMIS + ext+i, theta=0.25)",
+    "mesh": "unit cube, 32^3 cubes x 6 Kuhn tets, interior vertices jittered by <=0.2h (seed 0)",
+    "k": 3,
+    "n_h": 857375,
+    "l2_flush": "inputs larger than L2: A_h alone is 480 MB (12 B/nnz x 39,951,635 nnz) vs 129 MB L2",
+    "parallelism": "replicas (one independent solve per GPU)",
+}
+ORACLE_SAMPLE_ITERS = 12
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_problem():
+    from paper_1204_2586_gb300 import Problem
+    from paper_1204_2586_gb300.inputs import kuhn_mesh
+
+    xyz, t = kuhn_mesh(WORKLOAD["n"], WORKLOAD["jitter"], WORKLOAD["mesh_seed"])
+    return xyz, t, Problem(xyz, t, WORKLOAD["k"])
+
+
+def run_cpu_oracle(steps, warmup, sample_iters=ORACLE_SAMPLE_ITERS):
+    """The oracle, as it stands, on the host: assembly and setup untimed, then timed
+    bounded samples of the solve (sample_iters PCG iterations each)."""
+    import oracle
+    from paper_1204_2586_gb300.inputs import kuhn_mesh
+
+    xyz, t = kuhn_mesh(WORKLOAD["n"], WORKLOAD["jitter"], WORKLOAD["mesh_seed"])
+    P = oracle.Problem(xyz, t, WORKLOAD["k"])
+    P.setup(theta=0.25, max_iter=sample_iters)
+    times, iters = [], []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        out = P.solve()
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+            iters.append(out["iters"])
+    tot = sum(times)
+    value = P.nh * sum(iters) / tot / 1e6
+    return value, dict(value=value, unit=UNIT, cores=1, kind="oracle",
+                       sample=f"{steps} timed solves of {sample_iters} PCG iterations each on the full "
+                              f"workload (n_h={P.nh}); single-threaded C oracle, assembly/setup untimed",
+                       seconds=tot)
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    value, cpu = run_cpu_oracle(args.steps, args.warmup, sample_iters=4)
+    ms = cpu["seconds"] / args.steps * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1204_2586_gb300 import build
+
+    build.build()
+    t_as = time.perf_counter()
+    xyz, tets, G = make_problem()
+    torch.cuda.synchronize()
+    assemble_s = time.perf_counter() - t_as
+    t_su = time.perf_counter()
+    G.setup(theta=0.25)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_su
+    b = G.rhs()
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        x.zero_()
+        _, st = G.solve(b, x)
+        return st
+
+    for _ in range(args.warmup):
+        st = step()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, launches = [], 0
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = step()
+            iters.append(st["iters"][0])
+            launches += st["kernel_launches"]
+            assert st["status"][0] == 0, st
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    nh = G.nh
+    work = nh * sum(iters) * ws
+    value = work / (ms / 1e3) / 1e6
+    sol_s = ms / 1e3 / args.steps
+
+    # end to end through the C ABI with pinned host buffers: H2D of b and x0, D2H of x
+    bh = torch.empty(nh, dtype=torch.float64, pin_memory=True)
+    bh.copy_(b.cpu())
+    xh = torch.zeros(nh, dtype=torch.float64, pin_memory=True)
+    bnp, xnp = bh.numpy(), xh.numpy()
+    for _ in range(2):
+        xnp[:] = 0.0
+        G.solve(bnp, xnp)
+    torch.cuda.synchronize()
+    e_iters = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xnp[:] = 0.0
+        _, st = G.solve(bnp, xnp)
+        e_iters.append(st["iters"][0])
+    e2e_s = time.perf_counter() - t0
+    e2e_value = nh * sum(e_iters) * ws / e2e_s / 1e6
+
+    # roofline of the dominant kernel (the fine SpMV): algorithmic bytes per launch
+    # = 12 B per nonzero (FP64 value + int32 column) + 20 B per row (row pointer int64,
+    # x read once, y written) ; measured with CUDA events on the launching stream
+    spmv_ms = G.time_kernel(0, 50)
+    smoother_ms = G.time_kernel(1, 20)
+    nnz = int(G.info.nnz_h)
+    spmv_bytes = 12 * nnz + 20 * nh
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_spmv (fine A_h SpMV, FP64 CSR)", "achieved": achieved,
+            "peak": hbm if hbm else 6800.0, "unit": "GB/s",
+            "frac": achieved / (hbm if hbm else 6800.0), "traffic": None,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback",
+            "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms}
+    # one symmetric GS application from zero reads each off-diagonal entry once (value +
+    # column) and per row: diagonal, r, y (write, then read-modify-write), lptr/uptr, perm
+    smoother_bytes = 12 * (nnz - nh) + 52 * nh
+    extra = {"time_to_solution_s": sol_s, "iterations": iters[-1], "setup_s": setup_s,
+             "assemble_s": assemble_s, "levels": int(G.info.levels),
+             "level_rows": [int(v) for v in G.info.level_rows[: G.info.levels]],
+             "fine_colours": int(G.info.fine_colours), "op_complexity": G.info.op_complexity,
+             "smoother_ms": smoother_ms,
+             "smoother_GBps": smoother_bytes / (smoother_ms / 1e3) / 1e9}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            _, cpu = run_cpu_oracle(1, 0)
+            cpu.pop("seconds", None)
+        except Exception as e:  # the baseline must not sink the GPU line
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": CONFIG, "clocks": clk.summary(),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * nh,
+                        "d2h_bytes_per_step": 8 * nh},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu}
+        line.update(extra)
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

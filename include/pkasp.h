@@ -1,0 +1,267 @@
+/* pkasp.h -- C ABI of the GB300 library for auxiliary-space preconditioned conjugate
+ * gradients on P_k Lagrange discretisations of -div(kappa grad u) = f on tetrahedral
+ * meshes (Lee, Leng & Zhang, "A Scalable Auxiliary Space Preconditioner for High-Order
+ * Finite Element Methods", 2012; Xu's auxiliary space preconditioner B = S_k + Pi B_1 Pi^T).
+ *
+ * Equations are cited by the paper's consecutive numbering: Eq. (1) the model problem,
+ * Eq. (7) the linear system A_h u_h = f_h, Eq. (10) the transfer operators I_P = Pi and
+ * I_R = Pi^T; Algorithm 2.1 the two-level method; Remark 2.1 the symmetric (pre- and
+ * post-smoothed) form; Sec. 6.1-6.2 the AMG settings and the strength of connection.
+ *
+ * Conventions for every function:
+ *   - Return value: PKASP_OK (0) or a positive error code; pkasp_last_error() then
+ *     returns a message for the calling thread. No function aborts the process.
+ *   - Ownership: the library owns every pkasp_problem and all device memory it
+ *     allocates; pkasp_destroy frees both. The caller owns every array it passes in and
+ *     keeps it alive for the duration of the call only (nothing is retained).
+ *   - Pointers: arguments named *_host must be host memory; arguments named *_dev must
+ *     be device memory of the current device; arguments without a suffix may be either
+ *     (the library asks the CUDA driver which, and stages host data itself).
+ *   - Streams: every call that launches work takes a cudaStream_t (NULL = legacy
+ *     default stream). Calls return after enqueueing unless stated otherwise; calls that
+ *     return sizes or statistics synchronise the stream.
+ *   - Indices are 0-based. Dense vectors of several right-hand sides are row-major
+ *     [n][ld] with column c at offset c (ld >= ncols).
+ */
+#ifndef PKASP_H
+#define PKASP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so that callers need no CUDA headers. */
+typedef struct CUstream_st *pkasp_stream_t;
+
+typedef struct pkasp_problem pkasp_problem;
+
+enum {
+    PKASP_OK = 0,
+    PKASP_EINVAL = 1,     /* bad argument (size, degree, option value, null pointer) */
+    PKASP_EMESH = 2,      /* inverted or degenerate tetrahedron, bad vertex index */
+    PKASP_ENOMEM = 3,     /* device or host allocation failed, or a size limit hit */
+    PKASP_ENOTCONV = 4,   /* max_iter reached before the tolerance */
+    PKASP_EBREAKDOWN = 5, /* p^T A p <= 0 or a zero diagonal: the system is not SPD */
+    PKASP_ECUDA = 6,      /* a CUDA runtime call failed */
+    PKASP_ESTATE = 7      /* call out of order (e.g. solve before setup) */
+};
+
+enum { PKASP_MODE_ADDITIVE = 0, PKASP_MODE_MULTIPLICATIVE = 1 };
+enum { PKASP_SMOOTHER_SGS = 0, PKASP_SMOOTHER_L1JACOBI = 1 };
+enum { PKASP_PREC_FP64 = 0, PKASP_PREC_FP32 = 1 };
+enum { PKASP_SOURCE_NONE = 0, PKASP_SOURCE_SINE = 1 };
+enum { PKASP_MAX_LEVELS = 25, PKASP_MAX_COLS = 64 };
+
+/* Solver options (pkasp_default_options fills the defaults given in brackets). */
+typedef struct {
+    double theta;         /* strength threshold of Sec. 6.2 [0.25] */
+    int mode;             /* PKASP_MODE_*: additive z = S_k r + Pi V(Pi^T r) [additive];
+                             multiplicative = Algorithm 2.1 with pre-smoothing (Remark 2.1) */
+    int smoother;         /* P_k smoother S_k: PKASP_SMOOTHER_* [SGS: one forward and one
+                             backward multicolour Gauss-Seidel sweep, Remark 6.1] */
+    int level_smoother;   /* AMG level smoother, PKASP_SMOOTHER_* [SGS] */
+    int coarse_size;      /* stop coarsening at <= this many rows [256] */
+    int max_levels;       /* AMG levels including the coarsest, <= 25 [25] */
+    uint64_t seed;        /* seed of the colouring and PMIS hash streams [0] */
+    double tol;           /* stop when ||r_k||_2 <= tol ||r_0||_2 [1e-8] */
+    int max_iter;         /* [500] */
+    int flexible;         /* 1: flexible CG beta (z_new, r_new - r_old)/(z_old, r_old);
+                             forced on when precond_precision is FP32 [0] */
+    int precond_precision;/* PKASP_PREC_FP64 or PKASP_PREC_FP32: arithmetic of S_k, Pi and
+                             the whole AMG hierarchy; SpMV, dots, updates and the
+                             convergence test stay FP64 [FP64] */
+    int use_graph;        /* 1: each solve runs as one CUDA graph with a device-side
+                             while loop; 0: eager launches, host checks every iteration [1] */
+    int spmv_threads;     /* threads per row of the fine SpMV and smoother: 4, 8, 16 or
+                             32; 0 = pick by mean row length [0] */
+    int reserved[7];
+} pkasp_options;
+
+/* Problem sizes after assembly and (for the AMG entries) after setup. */
+typedef struct {
+    int64_t n_h, n_H;       /* P_k and P1 unknowns (Dirichlet nodes removed) */
+    int64_t nnz_h, nnz_H, nnz_pi;
+    int64_t n_all;          /* all P_k nodes including the boundary */
+    int64_t n_tets, n_verts;
+    int k;
+    int levels;             /* AMG levels (0 before setup) */
+    int fine_colours;       /* colours of the A_h graph (0 before setup) */
+    int coarse_rows;
+    int64_t level_rows[PKASP_MAX_LEVELS];
+    int64_t level_nnz[PKASP_MAX_LEVELS];
+    int level_colours[PKASP_MAX_LEVELS];
+    double op_complexity;   /* sum_l nnz(A_l) / nnz(A_H) (Sec. 6.2, Table 6) */
+    double setup_ms, assemble_ms;
+} pkasp_info;
+
+/* Per-solve statistics, filled by pkasp_solve (which synchronises the stream). */
+typedef struct {
+    int ncols;                          /* columns solved */
+    int iters[PKASP_MAX_COLS];          /* PCG iterations per column */
+    int status[PKASP_MAX_COLS];         /* PKASP_OK, PKASP_ENOTCONV or PKASP_EBREAKDOWN */
+    double true_rel[PKASP_MAX_COLS];    /* ||b - A x|| / ||b - A x0|| at exit */
+    double *hist_host;                  /* optional caller buffer [hist_cap][ncols]:
+                                           ||r_k||_2 after k iterations (k = 0..iters) */
+    int hist_cap;
+    int hist_len;                       /* rows written into hist_host */
+    int restarts;                       /* true-residual restarts taken (0 or 1) */
+    float solve_ms;                     /* device time of the solve (CUDA events) */
+    int64_t kernel_launches;            /* kernels of this library run by the solve */
+} pkasp_stats;
+
+/* ------------------------------------------------------------------------------------
+ * Construction
+ * ---------------------------------------------------------------------------------- */
+
+/* Fills *opt with the defaults listed in pkasp_options. */
+void pkasp_default_options(pkasp_options *opt);
+
+/* Message of the last failed call on this thread (always NUL-terminated). */
+int pkasp_last_error(char *buf, size_t n);
+
+/* Builds the P_k problem of Eq. (7) on a conforming tetrahedral mesh.
+ *   xyz_host   [nv][3] vertex coordinates
+ *   tets_host  [nt][4] vertex indices, positively oriented (det > 0)
+ *   k          polynomial degree, 1..4 (the paper's V_h = P^{k,0}, Sec. 2)
+ *   kappa      [nt] piecewise-constant coefficient, > 0 (host or device)
+ *   source     PKASP_SOURCE_SINE: load f_i = <f, phi_i> for f = 3 pi^2 sin(pi x)
+ *              sin(pi y) sin(pi z) by a degree 2k+3 Grundmann-Moeller rule;
+ *              PKASP_SOURCE_NONE: zero load (the caller passes its own b to solve).
+ * Dirichlet nodes (those on faces with one adjacent element) are removed (Eq. 1,
+ * u = 0 on the boundary). The DOF numbering is: vertices, then edges sorted by vertex
+ * pair (nodes from the lower vertex), then faces sorted by vertex triple (nodes in
+ * ascending multi-index order), then element interiors; unknowns keep that order.
+ * Assembles A_h (Eq. 7), the P1 matrix A_H of the same mesh and Pi = I_P (Eq. 10) on
+ * the device. Errors: EINVAL, EMESH (det <= 0, index out of range), ENOMEM, ECUDA.
+ * On success *out owns everything; release it with pkasp_destroy. */
+int pkasp_assemble(const double *xyz_host, int64_t nv, const int32_t *tets_host, int64_t nt,
+                   int k, const double *kappa, int source, pkasp_problem **out);
+
+/* Sizes and setup statistics (host struct). */
+int pkasp_problem_info(const pkasp_problem *p, pkasp_info *info);
+
+/* Numbering of the unknowns: dof_all_host[n_h] = index among all P_k nodes (the
+ * convention of pkasp_assemble) and dof_xyz_host[n_h][3] = node coordinates. Either may
+ * be NULL. */
+int pkasp_get_dofmap(const pkasp_problem *p, int64_t *dof_all_host, double *dof_xyz_host);
+
+/* Copies the assembled load vector f_h (Eq. 7) into b[n_h] (host or device). */
+int pkasp_get_rhs(const pkasp_problem *p, double *b, pkasp_stream_t stream);
+
+/* Replaces kappa [nt] (host or device, > 0) and re-assembles A_h, A_H and f_h on the
+ * same sparsity pattern. Invalidates the setup (call pkasp_setup again). */
+int pkasp_set_kappa(pkasp_problem *p, const double *kappa, pkasp_stream_t stream);
+
+/* Builds the preconditioner on the device: Jones-Plassmann colouring of A_h, strength
+ * graph (Sec. 6.2), PMIS C/F splitting, extended+i interpolation, Galerkin RAP per level
+ * (the relation A_H = I_R A_h I_P of Sec. 2 applied recursively), colourings of every
+ * level, the coarsest inverse, and FP32 copies when requested. Synchronises the stream.
+ * Errors: EINVAL (options), ENOMEM (coarsest level above 8192 rows), EBREAKDOWN
+ * (coarsest matrix not positive definite), ECUDA. */
+int pkasp_setup(pkasp_problem *p, const pkasp_options *opt, pkasp_stream_t stream);
+
+/* ------------------------------------------------------------------------------------
+ * Solve
+ * ---------------------------------------------------------------------------------- */
+
+/* Preconditioned CG on A_h x = b for ncols right-hand sides (1..64), columns
+ * independent (each converges, stops and is reported on its own). b and x are
+ * [n_h][ld] (host or device); x holds the initial guess on entry and the solution on
+ * exit. Stops when ||r_k|| <= tol ||r_0|| per column, then checks the true residual and
+ * restarts once if it is above tol. Fills *st (may be NULL) and synchronises the stream.
+ * Returns PKASP_OK when every column converged, else ENOTCONV or EBREAKDOWN (the
+ * per-column status is in *st), or EINVAL/ESTATE/ECUDA. */
+int pkasp_solve(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld,
+                pkasp_stats *st, pkasp_stream_t stream);
+
+/* Adjoint solve A_h^T lambda = g (A_h is symmetric, so this is the same operator and
+ * preconditioner): lambda holds the initial guess on entry. Same conventions as
+ * pkasp_solve. */
+int pkasp_solve_adjoint(pkasp_problem *p, const double *g, double *lambda, int ncols,
+                        int64_t ld, pkasp_stats *st, pkasp_stream_t stream);
+
+/* Element-wise gradient dL/dkappa_e = -lambda_e^T Khat_e u_e, Khat_e the element matrix
+ * of Eq. (7) with kappa_e = 1 (A_h is linear in kappa_e), for u, lambda [n_h] (device)
+ * and dkappa_dev [nt]. */
+int pkasp_grad_kappa(const pkasp_problem *p, const double *u_dev, const double *lambda_dev,
+                     double *dkappa_dev, pkasp_stream_t stream);
+
+/* Frees the problem and all its device memory. NULL is accepted. */
+int pkasp_destroy(pkasp_problem *p);
+
+/* ------------------------------------------------------------------------------------
+ * Operator access (for checks against an independent implementation and for tools).
+ * All vectors are device memory of n_h (or n_H) entries.
+ * ---------------------------------------------------------------------------------- */
+
+/* y = A_h x (Eq. 7). */
+int pkasp_spmv(const pkasp_problem *p, const double *x_dev, double *y_dev, pkasp_stream_t stream);
+
+/* z = B r with the preconditioner of the last pkasp_setup (FP64 or FP32 arithmetic). */
+int pkasp_apply_prec(pkasp_problem *p, const double *r_dev, double *z_dev, pkasp_stream_t stream);
+
+/* z = S_k r from a zero guess (the P_k smoother alone). */
+int pkasp_apply_smoother(pkasp_problem *p, const double *r_dev, double *z_dev,
+                         pkasp_stream_t stream);
+
+/* x = V(b): one AMG V(1,1)-cycle on A_H (b, x of n_H entries). */
+int pkasp_apply_vcycle(pkasp_problem *p, const double *b_dev, double *x_dev,
+                       pkasp_stream_t stream);
+
+/* Copies matrix `which` to host CSR arrays (any may be NULL); *nnz_out (may be NULL)
+ * receives the entry count. which: 0 A_h, 1 A_H, 2 Pi, 3 + 2l AMG level l matrix A_l,
+ * 4 + 2l the interpolation P_l of level l. Synchronises. ptr is [rows+1]. */
+int pkasp_get_matrix(const pkasp_problem *p, int which, int64_t *rows_out, int64_t *cols_out,
+                     int64_t *nnz_out, int64_t *ptr_host, int32_t *col_host, double *val_host);
+
+/* Colouring (colour per row) of A_h (level = -1) or of AMG level l; returns the count in
+ * *ncolours (may be NULL). */
+int pkasp_get_colours(const pkasp_problem *p, int level, int32_t *colour_host, int *ncolours);
+
+/* C/F splitting (+1 C, -1 F) and strength flags (one byte per entry of A_l) of AMG
+ * level l (not the coarsest). Either may be NULL. */
+int pkasp_get_splitting(const pkasp_problem *p, int level, int8_t *cf_host, uint8_t *strong_host);
+
+/* PMIS on a caller-supplied strength graph (De Sterck, Yang & Heys 2006, cited in Sec. 1
+ * and 6.1): CSR pattern ptr_dev[n+1], col_dev[nnz] of a structurally symmetric matrix
+ * with strong_dev[nnz] flags (1: column j is a strong connection of row i), hash stream
+ * `stream_id`; writes cf_dev[n] (+1 C, -1 F). Runs entirely on the device. */
+int pkasp_pmis(int64_t n, const int64_t *ptr_dev, const int32_t *col_dev,
+               const uint8_t *strong_dev, uint64_t stream_id, int8_t *cf_dev,
+               pkasp_stream_t stream);
+
+/* ------------------------------------------------------------------------------------
+ * Host-only helpers (no GPU needed): the numbering and sparsity patterns that
+ * pkasp_assemble builds, for checks and tools.
+ * ---------------------------------------------------------------------------------- */
+
+/* Sizes of the DOF map of a mesh (same arguments and conventions as pkasp_assemble):
+ * sizes_out[6] = {n_all, n_h, n_H, nnz(A_h), nnz(A_H), nnz(Pi)}. If the output arrays
+ * are non-NULL they are filled: dof_all_host[n_h], elem_dof_host[nt][nloc] (unknown index
+ * or -1 per local node, nloc = (k+1)(k+2)(k+3)/6, local nodes = multi-indices m of |m| =
+ * k in ascending lexicographic order), ah_ptr_host[n_h+1] / ah_col_host[nnz(A_h)] (the
+ * pattern of A_h), pi_ptr_host[n_h+1] / pi_col_host / pi_val_host (I_P of Eq. 10).
+ * Call once with NULL arrays to learn the sizes. Errors: EINVAL, EMESH. */
+int pkasp_dofmap_host(const double *xyz_host, int64_t nv, const int32_t *tets_host, int64_t nt, int k,
+                      int64_t *sizes_out, int64_t *dof_all_host, int32_t *elem_dof_host,
+                      int64_t *ah_ptr_host, int32_t *ah_col_host, int64_t *pi_ptr_host,
+                      int32_t *pi_col_host, double *pi_val_host);
+
+/* Reference tensors S[a][b][m][n] = (1/|T|) int_T (d phi_m/d lambda_a)(d phi_n/d lambda_b)
+ * of the degree-k Lagrange basis (S_out has 16 nloc^2 entries): the element matrix of
+ * Eq. (7) is kappa |T| sum_ab (grad lambda_a . grad lambda_b) S[a][b]. Host only. */
+int pkasp_reference_tensors(int k, double *S_out);
+
+/* Average device time (ms, CUDA events on `stream`) of `reps` back-to-back launches of
+ * one hot-path kernel of the current setup: which = 0 fine SpMV, 1 fine smoother
+ * (all colour phases of one S_k application), 2 V-cycle, 3 whole preconditioner. */
+int pkasp_time_kernel(pkasp_problem *p, int which, int reps, float *ms_out,
+                      pkasp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PKASP_H */

@@ -1,0 +1,233 @@
+// internal.h -- data structures shared by the translation units of libpkasp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pkasp.h"
+
+namespace pk {
+
+// ---------------------------------------------------------------------------------
+// Errors: every internal failure throws pk::Error; the C ABI layer converts it into a
+// status code and a per-thread message.
+// ---------------------------------------------------------------------------------
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string &msg);
+void cuda_check(cudaError_t e, const char *what, const char *file, int line);
+#define PK_CUDA(x) ::pk::cuda_check((x), #x, __FILE__, __LINE__)
+// every kernel launch of the library is followed by PK_LAUNCH(), which also counts it
+void launched(const char *file, int line);
+long long launch_count();
+#define PK_LAUNCH() ::pk::launched(__FILE__, __LINE__)
+
+// Device allocation tracked by the owning problem (freed in one place).
+struct DevPool {
+    std::vector<void *> blocks;
+    size_t bytes = 0;
+    void *alloc(size_t n);
+    void free_all();
+    template <class T>
+    T *get(size_t count) {
+        return static_cast<T *>(alloc(count * sizeof(T)));
+    }
+};
+
+// CSR matrix in device memory: int64 row pointers, int32 columns (sorted per row).
+struct DCSR {
+    int64_t n = 0, m = 0, nnz = 0;
+    int64_t *ptr = nullptr;
+    int32_t *col = nullptr;
+    double *val = nullptr;
+    float *val32 = nullptr;  // FP32 copy for the mixed-precision preconditioner
+};
+
+// Host CSR (setup and tests).
+struct HCSR {
+    int64_t n = 0, m = 0;
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> col;
+    std::vector<double> val;
+};
+
+// Rows of a matrix sorted by colour, each split into entries of lower colour (L),
+// higher colour (U) and the diagonal. Position p (0..n-1) in colour order holds row
+// perm[p]; colour c owns positions off[c]..off[c+1]-1.
+struct DSplit {
+    int ncol = 0;
+    std::vector<int64_t> off;  // host copy of the colour offsets
+    int32_t *colour = nullptr; // colour of each row (natural order)
+    int32_t *perm = nullptr;
+    int64_t *lptr = nullptr, *uptr = nullptr;
+    int32_t *lcol = nullptr, *ucol = nullptr;
+    double *lval = nullptr, *uval = nullptr, *diag = nullptr;
+    float *lval32 = nullptr, *uval32 = nullptr, *diag32 = nullptr;
+    int64_t nnz_l = 0, nnz_u = 0;
+};
+
+struct Level {
+    DCSR A;        // level matrix
+    DSplit sp;     // colour split of A
+    DCSR P, R;     // interpolation to the next level and its transpose
+    double *l1 = nullptr;  // row 1-norms
+    float *l132 = nullptr;
+    int8_t *cf = nullptr;        // C/F splitting (not on the coarsest)
+    uint8_t *strong = nullptr;   // strength flags per entry (not on the coarsest)
+    // work vectors (FP64 and FP32)
+    double *b = nullptr, *x = nullptr, *r = nullptr;
+    float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr;
+};
+
+// Scalars of one PCG run (device), per column.
+struct PcgState {
+    double rho[PKASP_MAX_COLS];
+    double alpha[PKASP_MAX_COLS];
+    double beta[PKASP_MAX_COLS];
+    double rnorm[PKASP_MAX_COLS];
+    double r0[PKASP_MAX_COLS];
+    int iter[PKASP_MAX_COLS];
+    int done[PKASP_MAX_COLS];
+    int status[PKASP_MAX_COLS];
+    double tnorm[PKASP_MAX_COLS];
+    int all_done;
+    int ncols;
+    int maxit;
+    int hist_cap;
+    int loops;
+    double tol;
+};
+
+}  // namespace pk
+
+// ---------------------------------------------------------------------------------
+// The problem handle.
+// ---------------------------------------------------------------------------------
+struct pkasp_problem {
+    pk::DevPool pool;       // assembly-lifetime memory
+    pk::DevPool setup_pool; // freed and rebuilt by every pkasp_setup
+    int device = 0;
+    int k = 0, nloc = 0;
+    int64_t nv = 0, nt = 0, n_all = 0, nh = 0, nH = 0;
+    int source = 0;
+    // host copies of the mesh and the DOF map
+    std::vector<double> xyz;
+    std::vector<int32_t> tets;
+    std::vector<int64_t> dof_all;   // [nh]
+    std::vector<double> dof_xyz;    // [nh*3]
+    std::vector<int32_t> elem_dof;  // [nt*nloc] unknown index or -1
+    std::vector<int32_t> elem_vdof; // [nt*4]
+    // device mesh data
+    double *d_xyz = nullptr, *d_kappa = nullptr;
+    int32_t *d_tets = nullptr, *d_elem_dof = nullptr, *d_elem_vdof = nullptr;
+    double *d_gfac = nullptr;  // [nt][17]: kappa|T| G_ab (16) and |T|
+    double *d_S = nullptr;     // reference tensors [16][nloc][nloc]
+    double *d_phiq = nullptr, *d_lamq = nullptr, *d_wq = nullptr;  // load quadrature
+    int nq = 0;
+    // incidence unknown -> (tet, local) in ascending tet order
+    int64_t *d_inc_ptr = nullptr, *d_vinc_ptr = nullptr;
+    int32_t *d_inc = nullptr, *d_vinc = nullptr;  // packed tet*64 + local
+    // operators
+    pk::DCSR Ah, AH, Pi, PiT;
+    double *d_b = nullptr;
+    double assemble_ms = 0, setup_ms = 0;
+    // setup
+    bool have_setup = false;
+    pkasp_options opt{};
+    pk::DSplit fine;      // colour split of A_h
+    double *d_l1h = nullptr;
+    float *d_l1h32 = nullptr;
+    std::vector<pk::Level> lev;
+    double *d_cinv = nullptr;  // dense inverse of the coarsest matrix
+    float *d_cinv32 = nullptr;
+    int64_t nc = 0;
+    int spmv_tpr = 8;
+    // solve work (sized for ncols = 1 at setup, grown on demand)
+    int work_cols = 0;
+    double *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_x = nullptr,
+           *w_b = nullptr, *w_zs = nullptr, *w_t = nullptr;
+    double *w_rr = nullptr;
+    float *w_zs32 = nullptr, *w_t32 = nullptr, *w_rr32 = nullptr;
+    cudaStream_t aux_stream = nullptr, cap_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int *d_flag = nullptr;
+    double *d_partials = nullptr;
+    unsigned int *d_counter = nullptr;
+    pk::PcgState *d_state = nullptr;
+    double *d_hist = nullptr;
+    int hist_cap = 0;
+    pk::DevPool work_pool;
+    // graph cache
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int graph_cols = 0;
+    long long g_init = 0, g_body = 0, g_final = 0;  // kernels per graph part
+    int64_t graph_ld = 0;
+    const void *graph_key_b = nullptr;
+    void *graph_key_x = nullptr;
+    cudaStream_t graph_stream = nullptr;
+};
+
+namespace pk {
+
+// ---- host side (mesh.cpp) -------------------------------------------------------
+struct HostMesh {
+    int k;
+    int64_t nv, nt;
+    const double *xyz;
+    const int32_t *tets;
+};
+struct DofMap {
+    int64_t n_all = 0, nh = 0, nH = 0;
+    std::vector<int64_t> dof_all;
+    std::vector<double> dof_xyz;
+    std::vector<int32_t> elem_dof, elem_vdof;
+    std::vector<int64_t> inc_ptr, vinc_ptr;
+    std::vector<int32_t> inc, vinc;  // tet*64 + local index
+    HCSR Ah_pattern, AH_pattern, Pi, PiT;
+};
+void build_dofmap(const HostMesh &m, DofMap &out);
+int nloc_of(int k);
+void ref_nodes(int k, std::vector<int> &m4);
+void reference_tensors(int k, std::vector<double> &S);          // [16][nloc][nloc]
+void gm_rule(int s, std::vector<double> &lam, std::vector<double> &w);
+void basis_values(int k, const double *lam, double *phi);
+
+// ---- device side ----------------------------------------------------------------
+void assemble_device(pkasp_problem *p, cudaStream_t s);
+void assemble_values(pkasp_problem *p, cudaStream_t s);
+void setup_device(pkasp_problem *p, cudaStream_t s);
+void free_setup(pkasp_problem *p);
+int solve_device(pkasp_problem *p, const double *b_dev, double *x_dev, int ncols, int64_t ld,
+                 pkasp_stats *st, cudaStream_t s);
+void apply_prec(pkasp_problem *p, const double *r, double *z, cudaStream_t s);
+void apply_smoother(pkasp_problem *p, const double *r, double *z, cudaStream_t s);
+void apply_vcycle(pkasp_problem *p, const double *b, double *x, cudaStream_t s);
+void spmv_fine(pkasp_problem *p, const double *x, double *y, cudaStream_t s);
+void grad_kappa_device(const pkasp_problem *p, const double *u, const double *lam, double *g,
+                       cudaStream_t s);
+void pmis_device(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_t *strong,
+                 uint64_t stream_id, int8_t *cf, cudaStream_t s);
+void ensure_work(pkasp_problem *p, int ncols);
+float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s);
+
+// small device utilities (util.cu)
+void to32(const double *x, float *y, int64_t n, cudaStream_t s);
+void exclusive_scan(int64_t *d, int64_t n, cudaStream_t s);  // in place, d[n] = total
+int64_t read_i64(const int64_t *d, cudaStream_t s);
+void dcsr_alloc(DevPool &pool, DCSR &a, int64_t n, int64_t m, int64_t nnz);
+void dcsr_upload(DevPool &pool, DCSR &a, const HCSR &h, cudaStream_t s);
+void dcsr_download(const DCSR &a, HCSR &h, cudaStream_t s);
+void dcsr_make32(DevPool &pool, DCSR &a, cudaStream_t s);
+
+// hash streams of the method's random choices
+inline uint64_t stream_colour(uint64_t seed, int m) { return seed * 64 + (uint64_t)m; }
+inline uint64_t stream_pmis(uint64_t seed, int l) { return seed * 64 + 32 + (uint64_t)l; }
+
+}  // namespace pk

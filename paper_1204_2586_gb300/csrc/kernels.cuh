@@ -1,0 +1,251 @@
+// kernels.cuh -- hot-path kernels of one PCG iteration: CSR SpMV, the colour phases of
+// the multicolour Gauss-Seidel smoothers, l1-Jacobi, the transfer operators I_P / I_R
+// (Eq. 10), the dense coarsest solve and the fused PCG vector updates.
+//
+// Rows are processed by sub-warps of TPR lanes (TPR in {4, 8, 16, 32}): the lanes of a
+// sub-warp stride over the row's entries, so the column and value loads of consecutive
+// lanes are coalesced, and the partial sums meet in a fixed xor-shuffle tree. Every
+// reduction uses a fixed grid and a fixed summation tree, so results are bitwise
+// reproducible from run to run.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace pk {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBlock = 256;
+constexpr int kRedGrid = 152 * 4;  // fixed grid of the reduction kernels
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) {
+    return __ldg(p);
+}
+
+// sum over the TPR lanes of a sub-warp (every lane of the warp must call this)
+template <int TPR, typename A>
+__device__ __forceinline__ A subwarp_sum(A v) {
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// sum_{e in [lo,hi)} val[e] * x[col[e]] accumulated in A by the lanes of a sub-warp
+template <int TPR, typename A, typename VT, typename XT>
+__device__ __forceinline__ A row_dot(int64_t lo, int64_t hi, int sub, const int32_t *__restrict__ col,
+                                     const VT *__restrict__ val, const XT *__restrict__ x) {
+    A acc = A(0);
+#pragma unroll 4
+    for (int64_t e = lo + sub; e < hi; e += TPR) acc += (A)ldg(&val[e]) * (A)ldg(&x[ldg(&col[e])]);
+    return subwarp_sum<TPR>(acc);
+}
+
+// ---------------------------------------------------------------------------------
+// Deterministic grid reduction: every block writes its partial sums, the last block
+// to arrive adds the partials in block order and returns true (in all its threads).
+// ---------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], double *partials, unsigned *counter,
+                                            double (&tot)[NV]) {
+    __shared__ double sh[NV][32];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if (lane == 0) sh[q][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[q][w];
+            partials[(int64_t)blockIdx.x * NV + q] = s;
+        }
+        __threadfence();
+        unsigned prev = atomicAdd(counter, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double x = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) x += __ldcg(&partials[(int64_t)b * NV + q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if (lane == 0) sh[q][wid] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sh[q][w];
+        tot[q] = s;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+// ---------------------------------------------------------------------------------
+// Plain CSR SpMV y = A x (transfer operators, level residual parts)
+// ---------------------------------------------------------------------------------
+template <int TPR, typename A, typename VT, typename XT, typename YT>
+__global__ void __launch_bounds__(kBlock) k_spmv(int64_t n, const int64_t *__restrict__ ptr,
+                                                 const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                                 const XT *__restrict__ x, YT *__restrict__ y) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = row < n;
+    int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+    A s = row_dot<TPR, A>(lo, hi, sub, col, val, x);
+    if (ok && sub == 0) y[row] = (YT)s;
+}
+
+// r = b - A x
+template <int TPR, typename A, typename VT, typename T>
+__global__ void __launch_bounds__(kBlock) k_residual(int64_t n, const int64_t *__restrict__ ptr,
+                                                     const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                                     const T *__restrict__ b, const T *__restrict__ x,
+                                                     T *__restrict__ r) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = row < n;
+    int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+    A s = row_dot<TPR, A>(lo, hi, sub, col, val, x);
+    if (ok && sub == 0) r[row] = (T)((A)b[row] - s);
+}
+
+// ---------------------------------------------------------------------------------
+// Multicolour Gauss-Seidel colour phases on a colour split (positions p in [pb, pe)
+// hold row perm[p]; L/U hold the entries of lower/higher colour).
+// forward from zero:   y_i = (r_i - sum_L a_ij y_j) / a_ii
+// backward from there: y_i = y_i - (sum_U a_ij y_j) / a_ii
+// backward full sweep: x_i = (b_i - sum_L a_ij x_j - sum_U a_ij x_j) / a_ii
+// ---------------------------------------------------------------------------------
+template <int TPR, typename PT, typename TR>
+__global__ void __launch_bounds__(kBlock) k_gs_fwd0(int64_t pb, int64_t pe, const int32_t *__restrict__ perm,
+                                                    const int64_t *__restrict__ lptr, const int32_t *__restrict__ lcol,
+                                                    const PT *__restrict__ lval, const PT *__restrict__ diag,
+                                                    const TR *__restrict__ r, PT *y) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = pb + gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = p < pe;
+    int64_t lo = ok ? lptr[p] : 0, hi = ok ? lptr[p + 1] : 0;
+    PT s = row_dot<TPR, PT>(lo, hi, sub, lcol, lval, (const PT *)y);
+    if (ok && sub == 0) {
+        int32_t i = perm[p];
+        y[i] = ((PT)r[i] - s) / diag[p];
+    }
+}
+
+template <int TPR, typename PT>
+__global__ void __launch_bounds__(kBlock) k_gs_bwd0(int64_t pb, int64_t pe, const int32_t *__restrict__ perm,
+                                                    const int64_t *__restrict__ uptr, const int32_t *__restrict__ ucol,
+                                                    const PT *__restrict__ uval, const PT *__restrict__ diag,
+                                                    PT *y) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = pb + gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = p < pe;
+    int64_t lo = ok ? uptr[p] : 0, hi = ok ? uptr[p + 1] : 0;
+    PT s = row_dot<TPR, PT>(lo, hi, sub, ucol, uval, (const PT *)y);
+    if (ok && sub == 0) {
+        int32_t i = perm[p];
+        y[i] = y[i] - s / diag[p];
+    }
+}
+
+template <int TPR, typename PT>
+__global__ void __launch_bounds__(kBlock) k_gs_bwd_full(int64_t pb, int64_t pe, const int32_t *__restrict__ perm,
+                                                        const int64_t *__restrict__ lptr, const int32_t *__restrict__ lcol,
+                                                        const PT *__restrict__ lval, const int64_t *__restrict__ uptr,
+                                                        const int32_t *__restrict__ ucol, const PT *__restrict__ uval,
+                                                        const PT *__restrict__ diag, const PT *__restrict__ b,
+                                                        PT *x) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = pb + gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = p < pe;
+    int64_t lo = ok ? lptr[p] : 0, hi = ok ? lptr[p + 1] : 0;
+    PT sl = row_dot<TPR, PT>(lo, hi, sub, lcol, lval, (const PT *)x);
+    lo = ok ? uptr[p] : 0;
+    hi = ok ? uptr[p + 1] : 0;
+    PT su = row_dot<TPR, PT>(lo, hi, sub, ucol, uval, (const PT *)x);
+    if (ok && sub == 0) {
+        int32_t i = perm[p];
+        x[i] = (b[i] - sl - su) / diag[p];
+    }
+}
+
+// l1-Jacobi: x = r / d (from zero) and x += (b - A x) / d
+template <typename PT, typename TR>
+__global__ void k_jacobi0(int64_t n, const PT *__restrict__ d, const TR *__restrict__ r, PT *__restrict__ x) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = (PT)r[i] / d[i];
+}
+
+template <int TPR, typename PT>
+__global__ void __launch_bounds__(kBlock) k_jacobi_step(int64_t n, const int64_t *__restrict__ ptr,
+                                                        const int32_t *__restrict__ col, const PT *__restrict__ val,
+                                                        const PT *__restrict__ d, const PT *__restrict__ b,
+                                                        const PT *__restrict__ xin, PT *__restrict__ xout) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = row < n;
+    int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+    PT s = row_dot<TPR, PT>(lo, hi, sub, col, val, xin);
+    if (ok && sub == 0) xout[row] = xin[row] + (b[row] - s) / d[row];
+}
+
+// z_i = zs_i + sum_j Pi_ij w_j (I_P has at most 4 entries per row: one thread per row)
+template <typename PT, typename ZT>
+__global__ void k_prolong_add(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                              const PT *__restrict__ val, const PT *__restrict__ w, const PT *zs, ZT *z) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PT s = PT(0);
+    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * w[col[e]];
+    z[i] = (ZT)zs[i] + (ZT)s;
+}
+
+// x_i += sum_j P_ij xc_j
+template <int TPR, typename PT>
+__global__ void __launch_bounds__(kBlock) k_prolong_inplace(int64_t n, const int64_t *__restrict__ ptr,
+                                                            const int32_t *__restrict__ col,
+                                                            const PT *__restrict__ val, const PT *__restrict__ xc,
+                                                            PT *__restrict__ x) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = row < n;
+    int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+    PT s = row_dot<TPR, PT>(lo, hi, sub, col, val, xc);
+    if (ok && sub == 0) x[row] += s;
+}
+
+// x = Ainv b for the dense inverse of the coarsest matrix (one warp per row)
+template <typename PT>
+__global__ void k_dense_mv(int64_t n, const PT *__restrict__ Ainv, const PT *__restrict__ b, PT *__restrict__ x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= n) return;  // whole warp leaves together
+    PT s = PT(0);
+    for (int64_t j = lane; j < n; j += 32) s += Ainv[row * n + j] * b[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if (lane == 0) x[row] = s;
+}
+
+}  // namespace pk

@@ -1,0 +1,842 @@
+// solve.cu -- the hot path: preconditioned conjugate gradients on A_h u = f_h (Eq. 7)
+// with the auxiliary-space preconditioner
+//     additive:       z = S_k r + I_P V(I_R r)
+//     multiplicative: Algorithm 2.1 with pre-smoothing (Remark 2.1)
+// where S_k is the multicolour symmetric Gauss-Seidel (or l1-Jacobi) smoother on A_h and
+// V one V(1,1)-cycle of the P1 AMG hierarchy. The two additive branches are independent
+// and run concurrently on two streams (two branches of the captured graph). One PCG
+// iteration is a fixed kernel sequence; the whole solve is captured once into a CUDA
+// graph whose while-node repeats the iteration until a device-side flag says stop.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace pk {
+
+void build_split(DevPool &pool, const DCSR &A, uint64_t stream, bool want32, DSplit &sp, cudaStream_t s);
+double *row_l1(DevPool &pool, const DCSR &A, cudaStream_t s);
+bool coarsen(DevPool &pool, Level &L, double theta, uint64_t pmis_stream, DCSR &Ac, cudaStream_t s);
+void coarse_inverse(DevPool &pool, const DCSR &A, double **inv, cudaStream_t s);
+
+namespace {
+
+// ---------------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------------
+int tpr_for(double mean_row) {
+    if (mean_row <= 6) return 4;
+    if (mean_row <= 20) return 8;
+    if (mean_row <= 56) return 16;
+    return 32;
+}
+int tpr_of(const DCSR &A) { return tpr_for(A.n > 0 ? (double)A.nnz / (double)A.n : 1.0); }
+
+unsigned rows_grid(int64_t rows, int tpr) {
+    int64_t threads = rows * tpr;
+    int64_t b = (threads + kBlock - 1) / kBlock;
+    return (unsigned)std::max<int64_t>(1, b);
+}
+unsigned elem_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + kBlock - 1) / kBlock); }
+
+template <typename PT>
+__global__ void k_copy_to(int64_t n, const PT *__restrict__ a, double *__restrict__ b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+template <typename PT>
+__global__ void k_to_pt(int64_t n, const double *__restrict__ a, PT *__restrict__ b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (PT)a[i];
+}
+
+template <typename PT>
+void to_pt(const double *a, PT *b, int64_t n, cudaStream_t s) {
+    k_to_pt<PT><<<elem_grid(n), kBlock, 0, s>>>(n, a, b);
+    PK_LAUNCH();
+}
+
+#define PK_TPR_SWITCH(tpr, BODY)                 \
+    switch (tpr) {                               \
+        case 4: { constexpr int TPR = 4; BODY; } break;   \
+        case 8: { constexpr int TPR = 8; BODY; } break;   \
+        case 16: { constexpr int TPR = 16; BODY; } break; \
+        default: { constexpr int TPR = 32; BODY; } break; \
+    }
+
+template <typename PT> const PT *pick(const double *d, const float *f);
+template <> const double *pick<double>(const double *d, const float *) { return d; }
+template <> const float *pick<float>(const double *, const float *f) { return f; }
+template <typename PT> PT *pickw(double *d, float *f);
+template <> double *pickw<double>(double *d, float *) { return d; }
+template <> float *pickw<float>(double *, float *f) { return f; }
+
+template <typename PT, typename A_, typename X, typename Y>
+void spmv(const DCSR &A, const X *x, Y *y, int tpr, cudaStream_t s) {
+    if (A.n == 0) return;
+    PK_TPR_SWITCH(tpr, (k_spmv<TPR, A_, PT><<<rows_grid(A.n, TPR), kBlock, 0, s>>>(
+                            A.n, A.ptr, A.col, pick<PT>(A.val, A.val32), x, y)));
+    PK_LAUNCH();
+}
+
+// colour phases of a forward sweep from zero: y = (D+L)^{-1} r
+template <typename PT, typename TR>
+void gs_forward0(const DSplit &sp, int tpr, const TR *r, PT *y, cudaStream_t s) {
+    for (int c = 0; c < sp.ncol; ++c) {
+        int64_t pb = sp.off[c], pe = sp.off[c + 1];
+        if (pe <= pb) continue;
+        PK_TPR_SWITCH(tpr, (k_gs_fwd0<TPR, PT, TR><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
+                                pb, pe, sp.perm, sp.lptr, sp.lcol, pick<PT>(sp.lval, sp.lval32),
+                                pick<PT>(sp.diag, sp.diag32), r, y)));
+        PK_LAUNCH();
+    }
+}
+
+// backward half of the symmetric sweep from zero: y <- y - D^{-1} U y, colours C-1..0
+template <typename PT>
+void gs_backward0(const DSplit &sp, int tpr, PT *y, cudaStream_t s) {
+    for (int c = sp.ncol - 1; c >= 0; --c) {
+        int64_t pb = sp.off[c], pe = sp.off[c + 1];
+        if (pe <= pb) continue;
+        PK_TPR_SWITCH(tpr, (k_gs_bwd0<TPR, PT><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
+                                pb, pe, sp.perm, sp.uptr, sp.ucol, pick<PT>(sp.uval, sp.uval32),
+                                pick<PT>(sp.diag, sp.diag32), y)));
+        PK_LAUNCH();
+    }
+}
+
+// full backward GS sweep on A x = b from the current x
+template <typename PT>
+void gs_backward_full(const DSplit &sp, int tpr, const PT *b, PT *x, cudaStream_t s) {
+    for (int c = sp.ncol - 1; c >= 0; --c) {
+        int64_t pb = sp.off[c], pe = sp.off[c + 1];
+        if (pe <= pb) continue;
+        PK_TPR_SWITCH(tpr, (k_gs_bwd_full<TPR, PT><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
+                                pb, pe, sp.perm, sp.lptr, sp.lcol, pick<PT>(sp.lval, sp.lval32), sp.uptr,
+                                sp.ucol, pick<PT>(sp.uval, sp.uval32), pick<PT>(sp.diag, sp.diag32), b, x)));
+        PK_LAUNCH();
+    }
+}
+
+template <typename PT>
+__global__ void k_add_div(int64_t n, const PT *__restrict__ r, const PT *__restrict__ d, PT *__restrict__ x) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += r[i] / d[i];
+}
+
+int split_tpr(const DSplit &sp, int64_t n) {
+    double m = n > 0 ? (double)std::max(sp.nnz_l, sp.nnz_u) / (double)n : 1.0;
+    return tpr_for(m);
+}
+
+// ---------------------------------------------------------------------------------
+// V(1,1)-cycle on level l (vectors b, x, r of each level)
+// ---------------------------------------------------------------------------------
+template <typename PT>
+PT *lv_b(Level &L) { return pickw<PT>(L.b, L.b32); }
+template <typename PT>
+PT *lv_x(Level &L) { return pickw<PT>(L.x, L.x32); }
+template <typename PT>
+PT *lv_r(Level &L) { return pickw<PT>(L.r, L.r32); }
+
+template <typename PT>
+void vcycle(pkasp_problem *p, int l, cudaStream_t s) {
+    Level &L = p->lev[l];
+    const int64_t n = L.A.n;
+    if (l == (int)p->lev.size() - 1) {
+        k_dense_mv<PT><<<rows_grid(n, 32), kBlock, 0, s>>>(n, pick<PT>(p->d_cinv, p->d_cinv32), lv_b<PT>(L),
+                                                          lv_x<PT>(L));
+        PK_LAUNCH();
+        return;
+    }
+    const bool jac = p->opt.level_smoother == PKASP_SMOOTHER_L1JACOBI;
+    const int ta = tpr_of(L.A), ts = split_tpr(L.sp, n);
+    if (jac) {
+        k_jacobi0<PT, PT><<<elem_grid(n), kBlock, 0, s>>>(n, pick<PT>(L.l1, L.l132), lv_b<PT>(L), lv_x<PT>(L));
+        PK_LAUNCH();
+    } else {
+        gs_forward0<PT, PT>(L.sp, ts, lv_b<PT>(L), lv_x<PT>(L), s);
+    }
+    PK_TPR_SWITCH(ta, (k_residual<TPR, PT, PT, PT><<<rows_grid(n, TPR), kBlock, 0, s>>>(
+                          n, L.A.ptr, L.A.col, pick<PT>(L.A.val, L.A.val32), lv_b<PT>(L), lv_x<PT>(L),
+                          lv_r<PT>(L))));
+    PK_LAUNCH();
+    Level &C = p->lev[l + 1];
+    spmv<PT, PT>(L.R, lv_r<PT>(L), lv_b<PT>(C), tpr_of(L.R), s);
+    vcycle<PT>(p, l + 1, s);
+    const int tp = tpr_of(L.P);
+    PK_TPR_SWITCH(tp, (k_prolong_inplace<TPR, PT><<<rows_grid(n, TPR), kBlock, 0, s>>>(
+                          n, L.P.ptr, L.P.col, pick<PT>(L.P.val, L.P.val32), lv_x<PT>(C), lv_x<PT>(L))));
+    PK_LAUNCH();
+    if (jac) {
+        PK_TPR_SWITCH(ta, (k_residual<TPR, PT, PT, PT><<<rows_grid(n, TPR), kBlock, 0, s>>>(
+                              n, L.A.ptr, L.A.col, pick<PT>(L.A.val, L.A.val32), lv_b<PT>(L), lv_x<PT>(L),
+                              lv_r<PT>(L))));
+        PK_LAUNCH();
+        k_add_div<PT><<<elem_grid(n), kBlock, 0, s>>>(n, lv_r<PT>(L), pick<PT>(L.l1, L.l132), lv_x<PT>(L));
+        PK_LAUNCH();
+    } else {
+        gs_backward_full<PT>(L.sp, ts, lv_b<PT>(L), lv_x<PT>(L), s);
+    }
+}
+
+// S_k r from zero into zs (PT)
+template <typename PT>
+void smoother(pkasp_problem *p, const double *r, PT *zs, cudaStream_t s) {
+    if (p->opt.smoother == PKASP_SMOOTHER_L1JACOBI) {
+        k_jacobi0<PT, double><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, pick<PT>(p->d_l1h, p->d_l1h32), r, zs);
+        PK_LAUNCH();
+        return;
+    }
+    const int ts = split_tpr(p->fine, p->nh);
+    gs_forward0<PT, double>(p->fine, ts, r, zs, s);
+    gs_backward0<PT>(p->fine, ts, zs, s);
+}
+
+template <typename PT>
+void restrict_vcycle(pkasp_problem *p, const double *r, cudaStream_t s) {
+    Level &L0 = p->lev[0];
+    spmv<PT, PT>(p->PiT, r, lv_b<PT>(L0), tpr_of(p->PiT), s);
+    vcycle<PT>(p, 0, s);
+}
+
+// z = B r
+template <typename PT>
+void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s) {
+    PT *zs = pickw<PT>(p->w_zs, p->w_zs32);
+    Level &L0 = p->lev[0];
+    if (p->opt.mode == PKASP_MODE_ADDITIVE) {
+        // fork: the V-cycle branch runs on the auxiliary stream, the smoother on s
+        PK_CUDA(cudaEventRecord(p->ev_fork, s));
+        PK_CUDA(cudaStreamWaitEvent(p->aux_stream, p->ev_fork, 0));
+        restrict_vcycle<PT>(p, r, p->aux_stream);
+        smoother<PT>(p, r, zs, s);
+        PK_CUDA(cudaEventRecord(p->ev_join, p->aux_stream));
+        PK_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+        k_prolong_add<PT, double><<<elem_grid(p->nh), kBlock, 0, s>>>(
+            p->nh, p->Pi.ptr, p->Pi.col, pick<PT>(p->Pi.val, p->Pi.val32), lv_x<PT>(L0), zs, z);
+        PK_LAUNCH();
+        return;
+    }
+    // multiplicative: forward GS (or l1 step) from zero, coarse correction of the new
+    // residual, backward GS sweep (or l1 step) from the corrected iterate
+    const bool jac = p->opt.smoother == PKASP_SMOOTHER_L1JACOBI;
+    const int ts = split_tpr(p->fine, p->nh);
+    const int ta = p->spmv_tpr;
+    PT *t = pickw<PT>(p->w_t, p->w_t32);
+    PT *rr = pickw<PT>(p->w_rr, p->w_rr32);
+    if (jac) {
+        k_jacobi0<PT, double><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, pick<PT>(p->d_l1h, p->d_l1h32), r, zs);
+        PK_LAUNCH();
+    } else {
+        gs_forward0<PT, double>(p->fine, ts, r, zs, s);
+    }
+    to_pt<PT>(r, rr, p->nh, s);
+    PK_TPR_SWITCH(ta, (k_residual<TPR, PT, PT, PT><<<rows_grid(p->nh, TPR), kBlock, 0, s>>>(
+                          p->nh, p->Ah.ptr, p->Ah.col, pick<PT>(p->Ah.val, p->Ah.val32), rr, zs, t)));
+    PK_LAUNCH();
+    spmv<PT, PT>(p->PiT, (const PT *)t, lv_b<PT>(L0), tpr_of(p->PiT), s);
+    vcycle<PT>(p, 0, s);
+    k_prolong_add<PT, PT><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, p->Pi.ptr, p->Pi.col,
+                                                              pick<PT>(p->Pi.val, p->Pi.val32), lv_x<PT>(L0),
+                                                              zs, zs);
+    PK_LAUNCH();
+    if (jac) {
+        PK_TPR_SWITCH(ta, (k_residual<TPR, PT, PT, PT><<<rows_grid(p->nh, TPR), kBlock, 0, s>>>(
+                              p->nh, p->Ah.ptr, p->Ah.col, pick<PT>(p->Ah.val, p->Ah.val32), rr, zs, t)));
+        PK_LAUNCH();
+        k_add_div<PT><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, t, pick<PT>(p->d_l1h, p->d_l1h32), zs);
+        PK_LAUNCH();
+    } else {
+        gs_backward_full<PT>(p->fine, ts, (const PT *)rr, zs, s);
+    }
+    k_copy_to<PT><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, zs, z);
+    PK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------------
+// PCG vector kernels (one right-hand side). Every kernel first reads the stop flag;
+// a stopped solve turns every later launch into a no-op, so extra iterations queued
+// behind the stop are harmless.
+// ---------------------------------------------------------------------------------
+enum { ST_RUN = -1 };
+
+__global__ void k_state_reset(PcgState *st, double tol, int maxit, int hist_cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    st->iter[0] = 0;
+    st->done[0] = 0;
+    st->status[0] = ST_RUN;
+    st->all_done = 0;
+    st->ncols = 1;
+    st->tol = tol;
+    st->maxit = maxit;
+    st->hist_cap = hist_cap;
+    st->loops = 0;
+    st->r0[0] = 0.0;
+}
+
+__global__ void k_state_restart(PcgState *st) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    st->done[0] = 0;
+    st->status[0] = ST_RUN;
+    st->all_done = 0;
+    st->loops = 0;
+}
+
+// r = b - A x, ||r||; on the first start also r0 and hist[0]
+template <int TPR>
+__global__ void __launch_bounds__(kBlock) k_init_residual(int64_t n, const int64_t *__restrict__ ptr,
+                                                          const int32_t *__restrict__ col,
+                                                          const double *__restrict__ val, const double *__restrict__ b,
+                                                          const double *__restrict__ x, double *__restrict__ r,
+                                                          PcgState *st, double *partials, unsigned *counter,
+                                                          double *hist) {
+    const int sub = threadIdx.x & (TPR - 1);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int rpw = 32 / TPR, sg = (threadIdx.x & 31) / TPR;
+    double part = 0.0;
+    for (int64_t base = warp * rpw; base < n; base += nwarps * rpw) {
+        const int64_t row = base + sg;
+        const bool ok = row < n;
+        int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+        double s = row_dot<TPR, double>(lo, hi, sub, col, val, x);
+        if (ok && sub == 0) {
+            double ri = b[row] - s;
+            r[row] = ri;
+            part += ri * ri;
+        }
+    }
+    double v[1] = {part}, tot[1];
+    if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+        double rn = sqrt(tot[0]);
+        st->rnorm[0] = rn;
+        if (st->iter[0] == 0) {
+            st->r0[0] = rn;
+            if (st->hist_cap > 0) hist[0] = rn;
+            if (rn == 0.0) {
+                st->done[0] = 1;
+                st->status[0] = PKASP_OK;
+                st->all_done = 1;
+            }
+        }
+    }
+}
+
+// p = z, rho = (r, z)
+__global__ void __launch_bounds__(kBlock) k_start(int64_t n, const double *__restrict__ r,
+                                                  const double *__restrict__ z, double *__restrict__ p,
+                                                  PcgState *st, double *partials, unsigned *counter) {
+    if (st->done[0]) return;
+    double part = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double zi = z[i];
+        p[i] = zi;
+        part += r[i] * zi;
+    }
+    double v[1] = {part}, tot[1];
+    if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) st->rho[0] = tot[0];
+}
+
+// q = A p, alpha = rho / (p, q)
+template <int TPR>
+__global__ void __launch_bounds__(kBlock) k_spmv_pq(int64_t n, const int64_t *__restrict__ ptr,
+                                                    const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                    const double *__restrict__ p, double *__restrict__ q,
+                                                    PcgState *st, double *partials, unsigned *counter) {
+    if (st->done[0]) return;
+    const int sub = threadIdx.x & (TPR - 1);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int rpw = 32 / TPR, sg = (threadIdx.x & 31) / TPR;
+    double part = 0.0;
+    for (int64_t base = warp * rpw; base < n; base += nwarps * rpw) {
+        const int64_t row = base + sg;
+        const bool ok = row < n;
+        int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+        double s = row_dot<TPR, double>(lo, hi, sub, col, val, p);
+        if (ok && sub == 0) {
+            q[row] = s;
+            part += p[row] * s;
+        }
+    }
+    double v[1] = {part}, tot[1];
+    if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+        double pq = tot[0];
+        if (!(pq > 0.0)) {
+            st->done[0] = 1;
+            st->status[0] = PKASP_EBREAKDOWN;
+            st->all_done = 1;
+        } else {
+            st->alpha[0] = st->rho[0] / pq;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q, ||r||, convergence test
+__global__ void __launch_bounds__(kBlock) k_update_xr(int64_t n, double *__restrict__ x, double *__restrict__ r,
+                                                      const double *__restrict__ p, const double *__restrict__ q,
+                                                      PcgState *st, double *partials, unsigned *counter,
+                                                      double *hist) {
+    if (st->done[0]) return;
+    const double a = st->alpha[0];
+    double part = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += a * p[i];
+        double ri = r[i] - a * q[i];
+        r[i] = ri;
+        part += ri * ri;
+    }
+    double v[1] = {part}, tot[1];
+    if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+        double rn = sqrt(tot[0]);
+        int it = st->iter[0] + 1;
+        st->iter[0] = it;
+        st->rnorm[0] = rn;
+        if (it < st->hist_cap) hist[it] = rn;
+        if (rn <= st->tol * st->r0[0]) {
+            st->done[0] = 1;
+            st->status[0] = PKASP_OK;
+            st->all_done = 1;
+        } else if (it >= st->maxit) {
+            st->done[0] = 1;
+            st->status[0] = PKASP_ENOTCONV;
+            st->all_done = 1;
+        }
+    }
+}
+
+// rho_new = (r, z); beta = rho_new / rho, or -alpha (z, q) / rho for flexible CG
+__global__ void __launch_bounds__(kBlock) k_beta(int64_t n, const double *__restrict__ r,
+                                                 const double *__restrict__ z, const double *__restrict__ q,
+                                                 int flexible, PcgState *st, double *partials, unsigned *counter) {
+    if (st->done[0]) return;
+    double a0 = 0.0, a1 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double zi = z[i];
+        a0 += r[i] * zi;
+        a1 += zi * q[i];
+    }
+    double v[2] = {a0, a1}, tot[2];
+    if (grid_reduce<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        double rho = st->rho[0];
+        st->beta[0] = flexible ? (-st->alpha[0] * tot[1]) / rho : tot[0] / rho;
+        st->rho[0] = tot[0];
+    }
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(kBlock) k_update_p(int64_t n, const double *__restrict__ z, double *__restrict__ p,
+                                                     const PcgState *st) {
+    if (st->done[0]) return;
+    const double b = st->beta[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + b * p[i];
+}
+
+// loop control of the captured while node: continue unless stopped; a safety bound on
+// the number of passes stops the loop even if no kernel set the flag
+__global__ void k_loop_control(PcgState *st, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int loops = ++st->loops;
+    bool go = !st->all_done && loops <= st->maxit + 2;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// true residual norm ||b - A x|| into st->tnorm
+template <int TPR>
+__global__ void __launch_bounds__(kBlock) k_true_residual(int64_t n, const int64_t *__restrict__ ptr,
+                                                          const int32_t *__restrict__ col,
+                                                          const double *__restrict__ val, const double *__restrict__ b,
+                                                          const double *__restrict__ x, PcgState *st,
+                                                          double *partials, unsigned *counter) {
+    const int sub = threadIdx.x & (TPR - 1);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int rpw = 32 / TPR, sg = (threadIdx.x & 31) / TPR;
+    double part = 0.0;
+    for (int64_t base = warp * rpw; base < n; base += nwarps * rpw) {
+        const int64_t row = base + sg;
+        const bool ok = row < n;
+        int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+        double s = row_dot<TPR, double>(lo, hi, sub, col, val, x);
+        if (ok && sub == 0) {
+            double ri = b[row] - s;
+            part += ri * ri;
+        }
+    }
+    double v[1] = {part}, tot[1];
+    if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) st->tnorm[0] = sqrt(tot[0]);
+}
+
+}  // namespace
+
+
+// ---------------------------------------------------------------------------------
+// setup orchestration
+// ---------------------------------------------------------------------------------
+void free_setup(pkasp_problem *p) {
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph_exec = nullptr;
+    p->graph = nullptr;
+    p->graph_key_b = nullptr;
+    p->graph_key_x = nullptr;
+    p->setup_pool.free_all();
+    p->work_pool.free_all();
+    p->lev.clear();
+    p->fine = DSplit{};
+    p->d_l1h = nullptr;
+    p->d_l1h32 = nullptr;
+    p->d_cinv = nullptr;
+    p->d_cinv32 = nullptr;
+    p->work_cols = 0;
+    p->have_setup = false;
+}
+
+void setup_device(pkasp_problem *p, cudaStream_t s) {
+    free_setup(p);
+    const pkasp_options &o = p->opt;
+    const bool want32 = o.precond_precision == PKASP_PREC_FP32;
+    DevPool &pool = p->setup_pool;
+    // fine level: colour split of A_h, l1 norms, FP32 copies
+    build_split(pool, p->Ah, stream_colour(o.seed, 0), want32, p->fine, s);
+    p->d_l1h = row_l1(pool, p->Ah, s);
+    if (want32) {
+        p->d_l1h32 = pool.get<float>(p->nh);
+        to32(p->d_l1h, p->d_l1h32, p->nh, s);
+        // FP32 copies of the assembled operators live as long as the problem; they are
+        // refreshed here because set_kappa may have changed A_h and A_H
+        for (DCSR *M : {&p->Ah, &p->AH, &p->Pi, &p->PiT}) {
+            if (!M->val32) dcsr_make32(p->pool, *M, s);
+            else to32(M->val, M->val32, M->nnz, s);
+        }
+    }
+    p->spmv_tpr = o.spmv_threads ? o.spmv_threads : tpr_of(p->Ah);
+    // P1 hierarchy
+    const int maxl = std::max(1, std::min(o.max_levels, (int)PKASP_MAX_LEVELS));
+    p->lev.clear();
+    p->lev.reserve(maxl);
+    p->lev.emplace_back();
+    p->lev[0].A = p->AH;  // level 0 aliases the assembled A_H (owned by the problem)
+    for (int l = 0;; ++l) {
+        Level &L = p->lev[l];
+        build_split(pool, L.A, stream_colour(o.seed, 1 + l), want32, L.sp, s);
+        L.l1 = row_l1(pool, L.A, s);
+        if (L.A.n <= o.coarse_size || l + 1 >= maxl) break;
+        DCSR Ac;
+        if (!coarsen(pool, L, o.theta, stream_pmis(o.seed, l), Ac, s)) break;
+        p->lev.emplace_back();
+        p->lev[l + 1].A = Ac;
+    }
+    Level &Lc = p->lev.back();
+    p->nc = Lc.A.n;
+    coarse_inverse(pool, Lc.A, &p->d_cinv, s);
+    // FP32 copies and per-level vectors
+    for (size_t l = 0; l < p->lev.size(); ++l) {
+        Level &L = p->lev[l];
+        const int64_t n = std::max<int64_t>(L.A.n, 1);
+        L.b = pool.get<double>(n);
+        L.x = pool.get<double>(n);
+        L.r = pool.get<double>(n);
+        if (want32) {
+            L.b32 = pool.get<float>(n);
+            L.x32 = pool.get<float>(n);
+            L.r32 = pool.get<float>(n);
+            if (l > 0) dcsr_make32(pool, L.A, s);
+            else L.A.val32 = p->AH.val32;
+            L.l132 = pool.get<float>(n);
+            to32(L.l1, L.l132, L.A.n, s);
+            if (L.P.n) {
+                dcsr_make32(pool, L.P, s);
+                dcsr_make32(pool, L.R, s);
+            }
+        }
+    }
+    if (want32) {
+        p->d_cinv32 = pool.get<float>(std::max<int64_t>(p->nc * p->nc, 1));
+        to32(p->d_cinv, p->d_cinv32, p->nc * p->nc, s);
+    }
+    if (!p->aux_stream) PK_CUDA(cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking));
+    if (!p->cap_stream) PK_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    if (!p->ev_fork) PK_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    if (!p->ev_join) PK_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    ensure_work(p, 1);
+    PK_CUDA(cudaStreamSynchronize(s));
+    p->have_setup = true;
+}
+
+void ensure_work(pkasp_problem *p, int ncols) {
+    if (p->work_cols >= ncols) return;
+    p->work_pool.free_all();
+    const int64_t n = std::max<int64_t>(p->nh, 1) * ncols;
+    DevPool &w = p->work_pool;
+    p->w_r = w.get<double>(n);
+    p->w_z = w.get<double>(n);
+    p->w_p = w.get<double>(n);
+    p->w_q = w.get<double>(n);
+    p->w_x = w.get<double>(n);
+    p->w_b = w.get<double>(n);
+    p->w_zs = w.get<double>(n);
+    p->w_t = w.get<double>(n);
+    p->w_rr = w.get<double>(n);
+    p->w_zs32 = w.get<float>(n);
+    p->w_t32 = w.get<float>(n);
+    p->w_rr32 = w.get<float>(n);
+    p->d_partials = w.get<double>((size_t)kRedGrid * 4 * PKASP_MAX_COLS);
+    p->d_counter = w.get<unsigned>(4);
+    PK_CUDA(cudaMemset(p->d_counter, 0, sizeof(unsigned) * 4));
+    p->d_state = w.get<PcgState>(1);
+    p->hist_cap = 0;
+    p->d_hist = nullptr;
+    p->work_cols = ncols;
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph_exec = nullptr;
+    p->graph = nullptr;
+}
+
+// ---------------------------------------------------------------------------------
+// public pieces
+// ---------------------------------------------------------------------------------
+void spmv_fine(pkasp_problem *p, const double *x, double *y, cudaStream_t s) {
+    spmv<double, double>(p->Ah, x, y, p->spmv_tpr ? p->spmv_tpr : tpr_of(p->Ah), s);
+}
+
+void apply_prec(pkasp_problem *p, const double *r, double *z, cudaStream_t s) {
+    if (p->opt.precond_precision == PKASP_PREC_FP32) precondition<float>(p, r, z, s);
+    else precondition<double>(p, r, z, s);
+}
+
+void apply_smoother(pkasp_problem *p, const double *r, double *z, cudaStream_t s) {
+    if (p->opt.precond_precision == PKASP_PREC_FP32) {
+        smoother<float>(p, r, p->w_zs32, s);
+        k_copy_to<float><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, p->w_zs32, z);
+    } else {
+        smoother<double>(p, r, z, s);
+    }
+    PK_LAUNCH();
+}
+
+void apply_vcycle(pkasp_problem *p, const double *b, double *x, cudaStream_t s) {
+    Level &L0 = p->lev[0];
+    const int64_t n = L0.A.n;
+    if (p->opt.precond_precision == PKASP_PREC_FP32) {
+        to_pt<float>(b, L0.b32, n, s);
+        vcycle<float>(p, 0, s);
+        k_copy_to<float><<<elem_grid(n), kBlock, 0, s>>>(n, L0.x32, x);
+    } else {
+        PK_CUDA(cudaMemcpyAsync(L0.b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        vcycle<double>(p, 0, s);
+        PK_CUDA(cudaMemcpyAsync(x, L0.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    PK_LAUNCH();
+}
+
+namespace {
+
+void enqueue_init(pkasp_problem *p, const double *b, double *x, cudaStream_t s) {
+    const int tpr = p->spmv_tpr;
+    PK_TPR_SWITCH(tpr, (k_init_residual<TPR><<<kRedGrid, kBlock, 0, s>>>(
+                           p->nh, p->Ah.ptr, p->Ah.col, p->Ah.val, b, x, p->w_r, p->d_state, p->d_partials,
+                           p->d_counter, p->d_hist)));
+    PK_LAUNCH();
+    apply_prec(p, p->w_r, p->w_z, s);
+    k_start<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_r, p->w_z, p->w_p, p->d_state, p->d_partials, p->d_counter);
+    PK_LAUNCH();
+}
+
+void enqueue_iteration(pkasp_problem *p, double *x, cudaStream_t s) {
+    const int tpr = p->spmv_tpr;
+    PK_TPR_SWITCH(tpr, (k_spmv_pq<TPR><<<kRedGrid, kBlock, 0, s>>>(p->nh, p->Ah.ptr, p->Ah.col, p->Ah.val,
+                                                                   p->w_p, p->w_q, p->d_state, p->d_partials,
+                                                                   p->d_counter)));
+    PK_LAUNCH();
+    k_update_xr<<<kRedGrid, kBlock, 0, s>>>(p->nh, x, p->w_r, p->w_p, p->w_q, p->d_state, p->d_partials,
+                                            p->d_counter, p->d_hist);
+    PK_LAUNCH();
+    apply_prec(p, p->w_r, p->w_z, s);
+    const int flex = (p->opt.flexible || p->opt.precond_precision == PKASP_PREC_FP32) ? 1 : 0;
+    k_beta<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_r, p->w_z, p->w_q, flex, p->d_state, p->d_partials,
+                                       p->d_counter);
+    PK_LAUNCH();
+    k_update_p<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_z, p->w_p, p->d_state);
+    PK_LAUNCH();
+}
+
+void enqueue_final(pkasp_problem *p, const double *b, const double *x, cudaStream_t s) {
+    const int tpr = p->spmv_tpr;
+    PK_TPR_SWITCH(tpr, (k_true_residual<TPR><<<kRedGrid, kBlock, 0, s>>>(
+                           p->nh, p->Ah.ptr, p->Ah.col, p->Ah.val, b, x, p->d_state, p->d_partials,
+                           p->d_counter)));
+    PK_LAUNCH();
+}
+
+void build_graph(pkasp_problem *p, const double *b, double *x) {
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph_exec = nullptr;
+    p->graph = nullptr;
+    cudaStream_t cs = p->cap_stream;
+    cudaGraph_t g, gi, gf;
+    PK_CUDA(cudaGraphCreate(&g, 0));
+    // init part
+    PK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    long long c0 = launch_count();
+    enqueue_init(p, b, x, cs);
+    p->g_init = launch_count() - c0;
+    PK_CUDA(cudaStreamEndCapture(cs, &gi));
+    cudaGraphNode_t ni, nc, nf;
+    PK_CUDA(cudaGraphAddChildGraphNode(&ni, g, nullptr, 0, gi));
+    // while loop over iterations
+    cudaGraphConditionalHandle h;
+    PK_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    PK_CUDA(cudaGraphAddNode(&nc, g, &ni, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    PK_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c0 = launch_count();
+    enqueue_iteration(p, x, cs);
+    k_loop_control<<<1, 32, 0, cs>>>(p->d_state, h);
+    PK_LAUNCH();
+    p->g_body = launch_count() - c0;
+    PK_CUDA(cudaStreamEndCapture(cs, &body));
+    // final true residual
+    PK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    c0 = launch_count();
+    enqueue_final(p, b, x, cs);
+    p->g_final = launch_count() - c0;
+    PK_CUDA(cudaStreamEndCapture(cs, &gf));
+    PK_CUDA(cudaGraphAddChildGraphNode(&nf, g, &nc, 1, gf));
+    PK_CUDA(cudaGraphInstantiate(&p->graph_exec, g, 0));
+    cudaGraphDestroy(gi);
+    cudaGraphDestroy(gf);
+    p->graph = g;
+}
+
+}  // namespace
+
+int solve_device(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld, pkasp_stats *st,
+                 cudaStream_t s) {
+    if (ncols != 1) fail(PKASP_EINVAL, "this build solves one right-hand side per call");
+    (void)ld;
+    ensure_work(p, 1);
+    const int cap = (st && st->hist_cap > 0) ? st->hist_cap : 1;
+    if (cap > p->hist_cap) {
+        p->d_hist = p->work_pool.get<double>(cap);
+        p->hist_cap = cap;
+        if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        p->graph_exec = nullptr;
+        p->graph = nullptr;
+    }
+    cudaEvent_t e0, e1;
+    PK_CUDA(cudaEventCreate(&e0));
+    PK_CUDA(cudaEventCreate(&e1));
+    k_state_reset<<<1, 32, 0, s>>>(p->d_state, p->opt.tol, p->opt.max_iter, p->hist_cap);
+    PK_LAUNCH();
+    PK_CUDA(cudaEventRecord(e0, s));
+    const bool use_graph = p->opt.use_graph != 0;
+    if (use_graph && (!p->graph_exec || p->graph_key_b != b || p->graph_key_x != x)) {
+        PK_CUDA(cudaStreamSynchronize(s));
+        build_graph(p, b, x);
+        p->graph_key_b = b;
+        p->graph_key_x = x;
+    }
+    PcgState hs;
+    int restarts = 0;
+    long long launches = 1;  // the state reset
+    const long long eager0 = launch_count();
+    for (;;) {
+        if (use_graph) {
+            PK_CUDA(cudaGraphLaunch(p->graph_exec, s));
+        } else {
+            enqueue_init(p, b, x, s);
+            for (int it = 0; it <= p->opt.max_iter + 1; ++it) {
+                enqueue_iteration(p, x, s);
+                int ad = 0;
+                PK_CUDA(cudaMemcpyAsync(&ad, &p->d_state->all_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+                PK_CUDA(cudaStreamSynchronize(s));
+                if (ad) break;
+            }
+            enqueue_final(p, b, x, s);
+        }
+        PK_CUDA(cudaMemcpyAsync(&hs, p->d_state, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+        PK_CUDA(cudaStreamSynchronize(s));
+        if (use_graph) launches += p->g_init + (long long)hs.loops * p->g_body + p->g_final;
+        const bool conv = hs.status[0] == PKASP_OK;
+        if (conv && hs.r0[0] > 0 && hs.tnorm[0] > p->opt.tol * hs.r0[0] && restarts == 0 &&
+            hs.iter[0] < p->opt.max_iter) {
+            ++restarts;
+            k_state_restart<<<1, 32, 0, s>>>(p->d_state);
+            PK_LAUNCH();
+            continue;
+        }
+        break;
+    }
+    PK_CUDA(cudaEventRecord(e1, s));
+    PK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int status = hs.status[0];
+    if (status == ST_RUN) status = PKASP_ENOTCONV;
+    if (st) {
+        st->ncols = 1;
+        st->iters[0] = hs.iter[0];
+        st->status[0] = status;
+        st->true_rel[0] = hs.r0[0] > 0 ? hs.tnorm[0] / hs.r0[0] : 0.0;
+        st->restarts = restarts;
+        st->solve_ms = ms;
+        st->kernel_launches = use_graph ? launches + restarts : 1 + (launch_count() - eager0);
+        st->hist_len = std::min(hs.iter[0] + 1, st->hist_cap);
+        if (st->hist_host && st->hist_len > 0)
+            PK_CUDA(cudaMemcpy(st->hist_host, p->d_hist, sizeof(double) * st->hist_len, cudaMemcpyDeviceToHost));
+    }
+    return status;
+}
+
+float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s) {
+    if (reps < 1) reps = 1;
+    cudaEvent_t e0, e1;
+    PK_CUDA(cudaEventCreate(&e0));
+    PK_CUDA(cudaEventCreate(&e1));
+    // inputs: r = f_h in w_r, p-vector = f_h
+    PK_CUDA(cudaMemcpyAsync(p->w_r, p->d_b, sizeof(double) * p->nh, cudaMemcpyDeviceToDevice, s));
+    PK_CUDA(cudaMemcpyAsync(p->w_p, p->d_b, sizeof(double) * p->nh, cudaMemcpyDeviceToDevice, s));
+    auto once = [&]() {
+        switch (which) {
+            case 0: spmv_fine(p, p->w_p, p->w_q, s); break;
+            case 1: {
+                if (p->opt.precond_precision == PKASP_PREC_FP32) smoother<float>(p, p->w_r, p->w_zs32, s);
+                else smoother<double>(p, p->w_r, p->w_zs, s);
+                break;
+            }
+            case 2: {
+                if (p->opt.precond_precision == PKASP_PREC_FP32) restrict_vcycle<float>(p, p->w_r, s);
+                else restrict_vcycle<double>(p, p->w_r, s);
+                break;
+            }
+            default: apply_prec(p, p->w_r, p->w_z, s); break;
+        }
+    };
+    for (int i = 0; i < 3; ++i) once();
+    PK_CUDA(cudaEventRecord(e0, s));
+    for (int i = 0; i < reps; ++i) once();
+    PK_CUDA(cudaEventRecord(e1, s));
+    PK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / reps;
+}
+
+}  // namespace pk

@@ -1,0 +1,126 @@
+"""GPU edge cases and failure reporting through the C ABI: degenerate meshes, ragged
+sizes, non-convergence, indefinite input, inverted elements. Every failure is a status
+code from the host or a device flag the host reads; nothing faults or hangs the GPU."""
+import numpy as np
+import pytest
+
+from paper_1204_2586_gb300.inputs import kappa_lognormal, kuhn_mesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1204_2586_gb300 import build
+
+    build.build()
+    return torch
+
+
+def test_single_cube_has_no_p1_unknown(gpu):
+    from paper_1204_2586_gb300 import PkaspError, Problem
+    from paper_1204_2586_gb300 import _lib as L
+
+    xyz, t = kuhn_mesh(1, 0.0, 0)
+    with pytest.raises(PkaspError) as e:
+        Problem(xyz, t, 2)
+    assert e.value.code == L.PKASP_EINVAL
+
+
+def test_inverted_element_is_reported(gpu):
+    from paper_1204_2586_gb300 import PkaspError, Problem
+    from paper_1204_2586_gb300 import _lib as L
+
+    xyz, t = kuhn_mesh(3, 0.2, 0)
+    t = t.copy()
+    t[10, [2, 3]] = t[10, [3, 2]]
+    with pytest.raises(PkaspError) as e:
+        Problem(xyz, t, 2)
+    assert e.value.code == L.PKASP_EMESH
+
+
+def test_not_converged_status(gpu):
+    from paper_1204_2586_gb300 import Problem
+    from paper_1204_2586_gb300 import _lib as L
+
+    xyz, t = kuhn_mesh(4, 0.2, 0)
+    G = Problem(xyz, t, 3)
+    for graph in (1, 0):
+        G.setup(max_iter=2, use_graph=graph)
+        x, st = G.solve(G.rhs(), raise_on_fail=False)
+        assert st["rc"] == L.PKASP_ENOTCONV and st["status"][0] == L.PKASP_ENOTCONV
+        assert st["iters"][0] == 2
+    G.close()
+
+
+def test_indefinite_matrix_is_reported(gpu):
+    """kappa < 0 everywhere makes A_h negative definite: either the coarsest Cholesky
+    (setup) or the first p^T A p (solve) reports a breakdown."""
+    from paper_1204_2586_gb300 import PkaspError, Problem
+    from paper_1204_2586_gb300 import _lib as L
+
+    xyz, t = kuhn_mesh(3, 0.2, 0)
+    G = Problem(xyz, t, 2, kappa=-np.ones(t.shape[0]))
+    try:
+        G.setup()
+    except PkaspError as e:
+        assert e.code == L.PKASP_EBREAKDOWN
+        return
+    x, st = G.solve(G.rhs(), raise_on_fail=False)
+    assert st["status"][0] == L.PKASP_EBREAKDOWN
+    G.close()
+
+
+def test_zero_rhs_converges_immediately(gpu):
+    torch = gpu
+    from paper_1204_2586_gb300 import Problem
+
+    xyz, t = kuhn_mesh(3, 0.2, 0)
+    G = Problem(xyz, t, 2)
+    G.setup()
+    b = torch.zeros(G.nh, dtype=torch.float64, device="cuda")
+    x, st = G.solve(b)
+    assert st["status"][0] == 0 and st["iters"][0] == 0
+    assert float(x.abs().max()) == 0.0
+    G.close()
+
+
+@pytest.mark.parametrize("k,n", [(1, 4), (2, 2), (4, 2), (3, 7)])
+def test_ragged_sizes_match_oracle(gpu, oracle_mod, k, n):
+    """Sizes that leave partial sub-warps, blocks and colour phases everywhere."""
+    xyz, t = kuhn_mesh(n, 0.2, 3)
+    kap = kappa_lognormal(t.shape[0], 5)
+    from paper_1204_2586_gb300 import Problem
+
+    G = Problem(xyz, t, k, kap)
+    G.setup(coarse_size=8)
+    O = oracle_mod.Problem(xyz, t, k, kap)
+    O.setup(coarse_size=8)
+    ref = O.solve()
+    x, st = G.solve(G.rhs(), hist_cap=600)
+    assert abs(st["iters"][0] - ref["iters"]) <= 1
+    m = min(len(ref["hist"]), st["hist"].shape[0])
+    assert (np.abs(st["hist"][:m, 0] - ref["hist"][:m]) / ref["hist"][0]).max() <= 1e-10
+    G.close()
+
+
+def test_set_kappa_reassembles(gpu, oracle_mod):
+    from paper_1204_2586_gb300 import Problem
+
+    xyz, t = kuhn_mesh(4, 0.2, 0)
+    G = Problem(xyz, t, 3)
+    k2 = kappa_lognormal(t.shape[0], 7)
+    G.set_kappa(k2)
+    O = oracle_mod.Problem(xyz, t, 3, k2)
+    _, _, val, _ = G.matrix(0)
+    ov = O.matrix(0).val
+    assert np.abs(val - ov).max() <= 1e-12 * np.abs(ov).max()
+    G.setup()
+    O.setup()
+    x, st = G.solve(G.rhs(), hist_cap=600)
+    ref = O.solve()
+    assert abs(st["iters"][0] - ref["iters"]) <= 1
+    G.close()

@@ -1,0 +1,70 @@
+"""Full-size parity on the benchmarked workload (P3, 32^3 jittered Kuhn cubes, 857,375
+unknowns) in the launch configuration bench.py times: the oracle runs the same solve on
+the host (about a minute), and the GPU must reproduce its integer decisions exactly and
+its residual history per iteration."""
+import numpy as np
+import pytest
+
+from paper_1204_2586_gb300.inputs import kuhn_mesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fullsize(oracle_mod):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1204_2586_gb300 import Problem, build
+
+    build.build()
+    xyz, t = kuhn_mesh(32, 0.2, 0)
+    G = Problem(xyz, t, 3)
+    G.setup(theta=0.25)
+    O = oracle_mod.Problem(xyz, t, 3)
+    O.setup(theta=0.25)
+    yield G, O
+    G.close()
+
+
+def test_fullsize_operators_sampled(fullsize):
+    G, O = fullsize
+    assert (G.nh, G.nH) == (857375, 29791)
+    gptr, gcol, gval, _ = G.matrix(0)
+    A = O.matrix(0)
+    assert np.array_equal(gptr, A.ptr) and np.array_equal(gcol, A.col)
+    rows = np.random.default_rng(0).choice(G.nh, 4000, replace=False)
+    for i in rows:
+        lo, hi = A.ptr[i], A.ptr[i + 1]
+        assert np.allclose(gval[lo:hi], A.val[lo:hi], rtol=1e-12, atol=1e-12 * np.abs(A.val[lo:hi]).max())
+    b = G.rhs().cpu().numpy()
+    bo = O.rhs()
+    assert np.abs(b - bo).max() <= 1e-12 * np.abs(bo).max()
+
+
+def test_fullsize_integer_decisions(fullsize):
+    G, O = fullsize
+    assert np.array_equal(G.colours(-1)[0], O.fine_colour())
+    assert G.info.levels == O.levels()
+    for l in range(O.levels()):
+        Lo = O.level(l)
+        assert np.array_equal(G.colours(l)[0], Lo["colour"])
+        if "cf" in Lo:
+            cf, st = G.splitting(l)
+            assert np.array_equal(cf, Lo["cf"]) and np.array_equal(st, Lo["strong"])
+
+
+def test_fullsize_pcg_history(fullsize):
+    G, O = fullsize
+    ref = O.solve()
+    assert ref["status"] == 0
+    x, st = G.solve(G.rhs(), hist_cap=600)
+    assert st["status"][0] == 0 and abs(st["iters"][0] - ref["iters"]) <= 1
+    h = st["hist"][:, 0]
+    m = min(len(h), len(ref["hist"]))
+    assert (np.abs(h[:m] - ref["hist"][:m]) / ref["hist"][0]).max() <= 1e-10
+    assert st["true_rel"][0] <= 1e-8
+    # sampled solution entries against the oracle's solution
+    idx = np.random.default_rng(1).choice(G.nh, 5000, replace=False)
+    xs = x.cpu().numpy()
+    assert np.abs(xs[idx] - ref["x"][idx]).max() <= 1e-8 * np.abs(ref["x"]).max()
