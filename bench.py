@@ -159,6 +159,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch the same kernels without the CUDA graph (profilers cannot see "
+                         "kernels inside graphs that hold conditional nodes)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -182,7 +185,7 @@ def main():
     torch.cuda.synchronize()
     assemble_s = time.perf_counter() - t_as
     t_su = time.perf_counter()
-    G.setup(theta=0.25)
+    G.setup(theta=0.25, use_graph=0 if args.eager else 1)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_su
     b = G.rhs()

@@ -95,6 +95,9 @@ typedef struct {
     int level_colours[PKASP_MAX_LEVELS];
     double op_complexity;   /* sum_l nnz(A_l) / nnz(A_H) (Sec. 6.2, Table 6) */
     double setup_ms, assemble_ms;
+    int spmv_layout;        /* autotuned layout of the fine SpMV: 0 = SELL-32 (one thread
+                               per row), t > 0 = CSR read by t lanes per row */
+    int smoother_layout;    /* same for the fine smoother's colour phases */
 } pkasp_info;
 
 /* Per-solve statistics, filled by pkasp_solve (which synchronises the stream). */

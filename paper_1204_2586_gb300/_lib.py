@@ -38,7 +38,8 @@ class pkasp_info(C.Structure):
                 ("fine_colours", C.c_int), ("coarse_rows", C.c_int),
                 ("level_rows", C.c_int64 * MAX_LEVELS), ("level_nnz", C.c_int64 * MAX_LEVELS),
                 ("level_colours", C.c_int * MAX_LEVELS), ("op_complexity", C.c_double),
-                ("setup_ms", C.c_double), ("assemble_ms", C.c_double)]
+                ("setup_ms", C.c_double), ("assemble_ms", C.c_double),
+                ("spmv_layout", C.c_int), ("smoother_layout", C.c_int)]
 
 
 class pkasp_stats(C.Structure):

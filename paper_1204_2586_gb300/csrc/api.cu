@@ -186,6 +186,8 @@ int pkasp_problem_info(const pkasp_problem *p, pkasp_info *info) {
         }
         info->op_complexity = p->AH.nnz > 0 ? tot / (double)p->AH.nnz : 0;
         info->setup_ms = p->setup_ms;
+        info->spmv_layout = p->spmv_tpr;
+        info->smoother_layout = p->fine_tpr;
     }
     return PKASP_OK;
 }

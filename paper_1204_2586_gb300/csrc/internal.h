@@ -70,6 +70,24 @@ struct DSplit {
     double *lval = nullptr, *uval = nullptr, *diag = nullptr;
     float *lval32 = nullptr, *uval32 = nullptr, *diag32 = nullptr;
     int64_t nnz_l = 0, nnz_u = 0;
+    std::vector<int> lmax, umax;  // per colour: longest lower / upper part (host)
+};
+
+// SELL-32: slices of 32 rows (one thread per row), entries column-major within a slice
+// (entry k of slice row r at sptr[slice] + 32 k + r), padded with column -1. perm maps
+// a padded position to its row (natural order when null; -1 marks padding rows); coff
+// gives each colour's slice range when the rows are colour-sorted.
+struct DSell {
+    int64_t nslices = 0, npos = 0, nnz_padded = 0;
+    int32_t *perm = nullptr;
+    int64_t *sptr = nullptr;
+    int32_t *swidth = nullptr;
+    int32_t *col = nullptr;
+    double *val = nullptr;
+    float *val32 = nullptr;
+    double *diag = nullptr;
+    float *diag32 = nullptr;
+    std::vector<int64_t> coff;
 };
 
 struct Level {
@@ -141,13 +159,16 @@ struct pkasp_problem {
     bool have_setup = false;
     pkasp_options opt{};
     pk::DSplit fine;      // colour split of A_h
+    pk::DSell Asell;      // SELL-32 copy of A_h (natural order)
+    pk::DSell fsl, fsu;   // SELL-32 colour-sorted lower / upper parts of A_h
     double *d_l1h = nullptr;
     float *d_l1h32 = nullptr;
     std::vector<pk::Level> lev;
     double *d_cinv = nullptr;  // dense inverse of the coarsest matrix
     float *d_cinv32 = nullptr;
     int64_t nc = 0;
-    int spmv_tpr = 8;
+    int spmv_tpr = 4;   // lanes per row of the fine SpMV (autotuned at setup)
+    int fine_tpr = 4;   // lanes per row of the fine smoother phases (autotuned at setup)
     // solve work (sized for ncols = 1 at setup, grown on demand)
     int work_cols = 0;
     double *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_x = nullptr,
@@ -216,6 +237,11 @@ void pmis_device(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_
                  uint64_t stream_id, int8_t *cf, cudaStream_t s);
 void ensure_work(pkasp_problem *p, int ncols);
 float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s);
+
+// SELL-32 builders (sell.cu)
+void build_sell_natural(DevPool &pool, const DCSR &A, DSell &S, bool want32, cudaStream_t s);
+void build_sell_split(DevPool &pool, const DSplit &sp, int64_t n, bool upper, DSell &S, bool want32,
+                      cudaStream_t s);
 
 // small device utilities (util.cu)
 void to32(const double *x, float *y, int64_t n, cudaStream_t s);

@@ -33,13 +33,31 @@ __device__ __forceinline__ A subwarp_sum(A v) {
     return v;
 }
 
-// sum_{e in [lo,hi)} val[e] * x[col[e]] accumulated in A by the lanes of a sub-warp
+// Entries per batch: a lane issues the column and value loads of kBatch entries (as
+// predicated loads) before the first dependent gather of x, so the whole batch's memory
+// traffic is in flight at once. Small colour phases are latency-bound and need this.
+constexpr int kBatch = 8;
+
+// sum_{e in [lo,hi)} val[e] * x[col[e]] accumulated in A by the lanes of a sub-warp,
+// lane `sub` adding entries lo+sub, lo+sub+TPR, ... in that order
 template <int TPR, typename A, typename VT, typename XT>
 __device__ __forceinline__ A row_dot(int64_t lo, int64_t hi, int sub, const int32_t *__restrict__ col,
                                      const VT *__restrict__ val, const XT *__restrict__ x) {
     A acc = A(0);
-#pragma unroll 4
-    for (int64_t e = lo + sub; e < hi; e += TPR) acc += (A)ldg(&val[e]) * (A)ldg(&x[ldg(&col[e])]);
+    for (int64_t base = lo + sub; base < hi; base += kBatch * TPR) {
+        int c[kBatch];
+        A v[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int64_t e = base + (int64_t)k * TPR;
+            const bool ok = e < hi;
+            c[k] = ok ? ldg(&col[e]) : -1;
+            v[k] = ok ? (A)ldg(&val[e]) : A(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k)
+            if (c[k] >= 0) acc += v[k] * (A)ldg(&x[c[k]]);
+    }
     return subwarp_sum<TPR>(acc);
 }
 
@@ -121,8 +139,9 @@ __global__ void __launch_bounds__(kBlock) k_residual(int64_t n, const int64_t *_
     const int sub = threadIdx.x & (TPR - 1);
     const bool ok = row < n;
     int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+    const A bi = (ok && sub == 0) ? (A)b[row] : A(0);
     A s = row_dot<TPR, A>(lo, hi, sub, col, val, x);
-    if (ok && sub == 0) r[row] = (T)((A)b[row] - s);
+    if (ok && sub == 0) r[row] = (T)(bi - s);
 }
 
 // ---------------------------------------------------------------------------------
@@ -137,16 +156,19 @@ __global__ void __launch_bounds__(kBlock) k_gs_fwd0(int64_t pb, int64_t pe, cons
                                                     const int64_t *__restrict__ lptr, const int32_t *__restrict__ lcol,
                                                     const PT *__restrict__ lval, const PT *__restrict__ diag,
                                                     const TR *__restrict__ r, PT *y) {
+    // every per-row load that does not depend on the row sum is issued first, so the
+    // phase costs one round trip for them plus the entry loads and gathers
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t p = pb + gt / TPR;
     const int sub = threadIdx.x & (TPR - 1);
     const bool ok = p < pe;
+    const bool lead = ok && sub == 0;
+    const int32_t i = lead ? perm[p] : 0;
+    const PT d = lead ? diag[p] : PT(1);
     int64_t lo = ok ? lptr[p] : 0, hi = ok ? lptr[p + 1] : 0;
+    const PT ri = lead ? (PT)r[i] : PT(0);
     PT s = row_dot<TPR, PT>(lo, hi, sub, lcol, lval, (const PT *)y);
-    if (ok && sub == 0) {
-        int32_t i = perm[p];
-        y[i] = ((PT)r[i] - s) / diag[p];
-    }
+    if (lead) y[i] = (ri - s) / d;
 }
 
 template <int TPR, typename PT>
@@ -158,12 +180,13 @@ __global__ void __launch_bounds__(kBlock) k_gs_bwd0(int64_t pb, int64_t pe, cons
     const int64_t p = pb + gt / TPR;
     const int sub = threadIdx.x & (TPR - 1);
     const bool ok = p < pe;
+    const bool lead = ok && sub == 0;
+    const int32_t i = lead ? perm[p] : 0;
+    const PT d = lead ? diag[p] : PT(1);
     int64_t lo = ok ? uptr[p] : 0, hi = ok ? uptr[p + 1] : 0;
+    const PT yi = lead ? y[i] : PT(0);
     PT s = row_dot<TPR, PT>(lo, hi, sub, ucol, uval, (const PT *)y);
-    if (ok && sub == 0) {
-        int32_t i = perm[p];
-        y[i] = y[i] - s / diag[p];
-    }
+    if (lead) y[i] = yi - s / d;
 }
 
 template <int TPR, typename PT>
@@ -177,15 +200,15 @@ __global__ void __launch_bounds__(kBlock) k_gs_bwd_full(int64_t pb, int64_t pe, 
     const int64_t p = pb + gt / TPR;
     const int sub = threadIdx.x & (TPR - 1);
     const bool ok = p < pe;
-    int64_t lo = ok ? lptr[p] : 0, hi = ok ? lptr[p + 1] : 0;
-    PT sl = row_dot<TPR, PT>(lo, hi, sub, lcol, lval, (const PT *)x);
-    lo = ok ? uptr[p] : 0;
-    hi = ok ? uptr[p + 1] : 0;
-    PT su = row_dot<TPR, PT>(lo, hi, sub, ucol, uval, (const PT *)x);
-    if (ok && sub == 0) {
-        int32_t i = perm[p];
-        x[i] = (b[i] - sl - su) / diag[p];
-    }
+    const bool lead = ok && sub == 0;
+    const int32_t i = lead ? perm[p] : 0;
+    const PT d = lead ? diag[p] : PT(1);
+    const int64_t llo = ok ? lptr[p] : 0, lhi = ok ? lptr[p + 1] : 0;
+    const int64_t ulo = ok ? uptr[p] : 0, uhi = ok ? uptr[p + 1] : 0;
+    const PT bi = lead ? b[i] : PT(0);
+    PT sl = row_dot<TPR, PT>(llo, lhi, sub, lcol, lval, (const PT *)x);
+    PT su = row_dot<TPR, PT>(ulo, uhi, sub, ucol, uval, (const PT *)x);
+    if (lead) x[i] = (bi - sl - su) / d;
 }
 
 // l1-Jacobi: x = r / d (from zero) and x += (b - A x) / d
@@ -231,8 +254,9 @@ __global__ void __launch_bounds__(kBlock) k_prolong_inplace(int64_t n, const int
     const int sub = threadIdx.x & (TPR - 1);
     const bool ok = row < n;
     int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+    const PT xi = (ok && sub == 0) ? x[row] : PT(0);
     PT s = row_dot<TPR, PT>(lo, hi, sub, col, val, xc);
-    if (ok && sub == 0) x[row] += s;
+    if (ok && sub == 0) x[row] = xi + s;
 }
 
 // x = Ainv b for the dense inverse of the coarsest matrix (one warp per row)
@@ -246,6 +270,84 @@ __global__ void k_dense_mv(int64_t n, const PT *__restrict__ Ainv, const PT *__r
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
     if (lane == 0) x[row] = s;
+}
+
+// ---------------------------------------------------------------------------------
+// SELL-32 kernels: one thread per row; a warp is one slice, so every column and value
+// load of the warp is one contiguous access. Padding entries carry column -1.
+// ---------------------------------------------------------------------------------
+template <typename A, typename VT, typename XT>
+__device__ __forceinline__ A sell_dot(int64_t base, int w, const int32_t *__restrict__ col,
+                                      const VT *__restrict__ val, const XT *x) {
+    A acc = A(0);
+    for (int k0 = 0; k0 < w; k0 += kBatch) {
+        int c[kBatch];
+        A v[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int64_t e = base + 32 * (int64_t)(k0 + k);
+            const bool ok = k0 + k < w;
+            c[k] = ok ? __ldg(&col[e]) : -1;
+            v[k] = ok ? (A)__ldg(&val[e]) : A(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k)
+            if (c[k] >= 0) acc += v[k] * (A)x[c[k]];
+    }
+    return acc;
+}
+
+// y = A x, rows in natural order
+template <typename A, typename VT, typename XT, typename YT>
+__global__ void __launch_bounds__(kBlock) k_sell_spmv(int64_t n, const int64_t *__restrict__ sptr,
+                                                      const int32_t *__restrict__ sw, const int32_t *__restrict__ col,
+                                                      const VT *__restrict__ val, const XT *__restrict__ x,
+                                                      YT *__restrict__ y) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const int64_t s = row >> 5;
+    y[row] = (YT)sell_dot<A>(sptr[s] + (row & 31), sw[s], col, val, x);
+}
+
+// colour phase of the forward sweep from zero over slices [s0, s1):
+//   y_i = (r_i - sum_L a_ij y_j) / a_ii
+template <typename PT, typename TR>
+__global__ void __launch_bounds__(kBlock) k_sell_gs_fwd0(int64_t s0, int64_t s1, const int32_t *__restrict__ perm,
+                                                         const int64_t *__restrict__ sptr,
+                                                         const int32_t *__restrict__ sw,
+                                                         const int32_t *__restrict__ col, const PT *__restrict__ val,
+                                                         const PT *__restrict__ diag, const TR *__restrict__ r,
+                                                         PT *y) {
+    const int64_t q = s0 * 32 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= s1 * 32) return;
+    const int64_t s = q >> 5;
+    // independent loads first; padding rows (perm < 0) have width-0 tails of column -1
+    const int32_t i = perm[q];
+    const int64_t base = sptr[s] + (q & 31);
+    const int w = sw[s];
+    const PT d = diag[q];
+    const PT ri = i >= 0 ? (PT)r[i] : PT(0);
+    const PT acc = sell_dot<PT>(base, w, col, val, (const PT *)y);
+    if (i >= 0) y[i] = (ri - acc) / d;
+}
+
+// colour phase of the backward sweep that follows: y_i <- y_i - (sum_U a_ij y_j) / a_ii
+template <typename PT>
+__global__ void __launch_bounds__(kBlock) k_sell_gs_bwd0(int64_t s0, int64_t s1, const int32_t *__restrict__ perm,
+                                                         const int64_t *__restrict__ sptr,
+                                                         const int32_t *__restrict__ sw,
+                                                         const int32_t *__restrict__ col, const PT *__restrict__ val,
+                                                         const PT *__restrict__ diag, PT *y) {
+    const int64_t q = s0 * 32 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= s1 * 32) return;
+    const int64_t s = q >> 5;
+    const int32_t i = perm[q];
+    const int64_t base = sptr[s] + (q & 31);
+    const int w = sw[s];
+    const PT d = diag[q];
+    const PT yi = i >= 0 ? y[i] : PT(0);
+    const PT acc = sell_dot<PT>(base, w, col, val, (const PT *)y);
+    if (i >= 0) y[i] = yi - acc / d;
 }
 
 }  // namespace pk

@@ -640,6 +640,21 @@ void build_split(DevPool &pool, const DCSR &A, uint64_t stream, bool want32, DSp
         exclusive_scan(sp.uptr, n, s);
         sp.nnz_l = read_i64(sp.lptr + n, s);
         sp.nnz_u = read_i64(sp.uptr + n, s);
+        {
+            // longest lower/upper part of each colour: it fixes the lanes per row of that
+            // colour's phase (one batch of loads per lane covers the whole row)
+            std::vector<int64_t> hl(n + 1), hu(n + 1);
+            PK_CUDA(cudaMemcpyAsync(hl.data(), sp.lptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+            PK_CUDA(cudaMemcpyAsync(hu.data(), sp.uptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+            PK_CUDA(cudaStreamSynchronize(s));
+            sp.lmax.assign(sp.ncol, 0);
+            sp.umax.assign(sp.ncol, 0);
+            for (int c = 0; c < sp.ncol; ++c)
+                for (int64_t q = sp.off[c]; q < sp.off[c + 1]; ++q) {
+                    sp.lmax[c] = std::max<int>(sp.lmax[c], (int)(hl[q + 1] - hl[q]));
+                    sp.umax[c] = std::max<int>(sp.umax[c], (int)(hu[q + 1] - hu[q]));
+                }
+        }
         sp.lcol = pool.get<int32_t>(sp.nnz_l > 0 ? sp.nnz_l : 1);
         sp.lval = pool.get<double>(sp.nnz_l > 0 ? sp.nnz_l : 1);
         sp.ucol = pool.get<int32_t>(sp.nnz_u > 0 ? sp.nnz_u : 1);

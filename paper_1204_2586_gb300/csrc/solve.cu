@@ -26,11 +26,12 @@ namespace {
 // ---------------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------------
+// Lanes per row. Short sub-warps keep more rows, and more independent loads per lane,
+// in flight: on GB300 four lanes beat sixteen by 1.7x on the P3 matrix (47 entries per
+// row). The fine SpMV and the fine smoother are autotuned at setup instead.
 int tpr_for(double mean_row) {
-    if (mean_row <= 6) return 4;
-    if (mean_row <= 20) return 8;
-    if (mean_row <= 56) return 16;
-    return 32;
+    if (mean_row <= 96) return 4;
+    return 8;
 }
 int tpr_of(const DCSR &A) { return tpr_for(A.n > 0 ? (double)A.nnz / (double)A.n : 1.0); }
 
@@ -61,6 +62,8 @@ void to_pt(const double *a, PT *b, int64_t n, cudaStream_t s) {
 
 #define PK_TPR_SWITCH(tpr, BODY)                 \
     switch (tpr) {                               \
+        case 1: { constexpr int TPR = 1; BODY; } break;   \
+        case 2: { constexpr int TPR = 2; BODY; } break;   \
         case 4: { constexpr int TPR = 4; BODY; } break;   \
         case 8: { constexpr int TPR = 8; BODY; } break;   \
         case 16: { constexpr int TPR = 16; BODY; } break; \
@@ -82,12 +85,23 @@ void spmv(const DCSR &A, const X *x, Y *y, int tpr, cudaStream_t s) {
     PK_LAUNCH();
 }
 
-// colour phases of a forward sweep from zero: y = (D+L)^{-1} r
+// Lanes per row for a colour phase whose longest row part has `len` entries: the fewest
+// lanes (a power of two, at most 32) for which one batch of loads per lane covers the row.
+// A colour phase is latency-bound, and every extra batch is one more DRAM round trip.
+int lanes_for(int len) {
+    int t = 1;
+    while (t < 32 && t * kBatch < len) t <<= 1;
+    return t;
+}
+
+// colour phases of a forward sweep from zero: y = (D+L)^{-1} r; tpr < 0 picks the lanes
+// per colour from the colour's longest lower part
 template <typename PT, typename TR>
-void gs_forward0(const DSplit &sp, int tpr, const TR *r, PT *y, cudaStream_t s) {
+void gs_forward0(const DSplit &sp, int tpr_fixed, const TR *r, PT *y, cudaStream_t s) {
     for (int c = 0; c < sp.ncol; ++c) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
+        const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(sp.lmax[c]);
         PK_TPR_SWITCH(tpr, (k_gs_fwd0<TPR, PT, TR><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
                                 pb, pe, sp.perm, sp.lptr, sp.lcol, pick<PT>(sp.lval, sp.lval32),
                                 pick<PT>(sp.diag, sp.diag32), r, y)));
@@ -97,10 +111,12 @@ void gs_forward0(const DSplit &sp, int tpr, const TR *r, PT *y, cudaStream_t s) 
 
 // backward half of the symmetric sweep from zero: y <- y - D^{-1} U y, colours C-1..0
 template <typename PT>
-void gs_backward0(const DSplit &sp, int tpr, PT *y, cudaStream_t s) {
-    for (int c = sp.ncol - 1; c >= 0; --c) {
+void gs_backward0(const DSplit &sp, int tpr_fixed, PT *y, cudaStream_t s) {
+    // the highest colour has no upper part: its phase would leave y unchanged
+    for (int c = sp.ncol - 2; c >= 0; --c) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
+        const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(sp.umax[c]);
         PK_TPR_SWITCH(tpr, (k_gs_bwd0<TPR, PT><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
                                 pb, pe, sp.perm, sp.uptr, sp.ucol, pick<PT>(sp.uval, sp.uval32),
                                 pick<PT>(sp.diag, sp.diag32), y)));
@@ -110,10 +126,11 @@ void gs_backward0(const DSplit &sp, int tpr, PT *y, cudaStream_t s) {
 
 // full backward GS sweep on A x = b from the current x
 template <typename PT>
-void gs_backward_full(const DSplit &sp, int tpr, const PT *b, PT *x, cudaStream_t s) {
+void gs_backward_full(const DSplit &sp, int tpr_fixed, const PT *b, PT *x, cudaStream_t s) {
     for (int c = sp.ncol - 1; c >= 0; --c) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
+        const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(std::max(sp.lmax[c], sp.umax[c]));
         PK_TPR_SWITCH(tpr, (k_gs_bwd_full<TPR, PT><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
                                 pb, pe, sp.perm, sp.lptr, sp.lcol, pick<PT>(sp.lval, sp.lval32), sp.uptr,
                                 sp.ucol, pick<PT>(sp.uval, sp.uval32), pick<PT>(sp.diag, sp.diag32), b, x)));
@@ -153,7 +170,7 @@ void vcycle(pkasp_problem *p, int l, cudaStream_t s) {
         return;
     }
     const bool jac = p->opt.level_smoother == PKASP_SMOOTHER_L1JACOBI;
-    const int ta = tpr_of(L.A), ts = split_tpr(L.sp, n);
+    const int ta = tpr_of(L.A), ts = -1;  // lanes per colour phase chosen per colour
     if (jac) {
         k_jacobi0<PT, PT><<<elem_grid(n), kBlock, 0, s>>>(n, pick<PT>(L.l1, L.l132), lv_b<PT>(L), lv_x<PT>(L));
         PK_LAUNCH();
@@ -191,7 +208,29 @@ void smoother(pkasp_problem *p, const double *r, PT *zs, cudaStream_t s) {
         PK_LAUNCH();
         return;
     }
-    const int ts = split_tpr(p->fine, p->nh);
+    const int ts = p->fine_tpr;
+    if (ts == 0) {
+        // SELL-32 colour phases: colour c is the slice range [coff[c], coff[c+1])
+        const DSell &L = p->fsl, &U = p->fsu;
+        const int nc = p->fine.ncol;
+        for (int c = 0; c < nc; ++c) {
+            const int64_t s0 = L.coff[c], s1 = L.coff[c + 1];
+            if (s1 <= s0) continue;
+            k_sell_gs_fwd0<PT, double><<<rows_grid((s1 - s0) * 32, 1), kBlock, 0, s>>>(
+                s0, s1, L.perm, L.sptr, L.swidth, L.col, pick<PT>(L.val, L.val32), pick<PT>(L.diag, L.diag32), r,
+                zs);
+            PK_LAUNCH();
+        }
+        // the highest colour has no upper part: its backward phase would leave y as is
+        for (int c = nc - 2; c >= 0; --c) {
+            const int64_t s0 = U.coff[c], s1 = U.coff[c + 1];
+            if (s1 <= s0) continue;
+            k_sell_gs_bwd0<PT><<<rows_grid((s1 - s0) * 32, 1), kBlock, 0, s>>>(
+                s0, s1, U.perm, U.sptr, U.swidth, U.col, pick<PT>(U.val, U.val32), pick<PT>(U.diag, U.diag32), zs);
+            PK_LAUNCH();
+        }
+        return;
+    }
     gs_forward0<PT, double>(p->fine, ts, r, zs, s);
     gs_backward0<PT>(p->fine, ts, zs, s);
 }
@@ -224,7 +263,7 @@ void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s) 
     // multiplicative: forward GS (or l1 step) from zero, coarse correction of the new
     // residual, backward GS sweep (or l1 step) from the corrected iterate
     const bool jac = p->opt.smoother == PKASP_SMOOTHER_L1JACOBI;
-    const int ts = split_tpr(p->fine, p->nh);
+    const int ts = p->fine_tpr > 0 ? p->fine_tpr : -1;  // the full backward sweep uses the CSR split
     const int ta = p->spmv_tpr;
     PT *t = pickw<PT>(p->w_t, p->w_t32);
     PT *rr = pickw<PT>(p->w_rr, p->w_rr32);
@@ -286,30 +325,58 @@ __global__ void k_state_restart(PcgState *st) {
     st->loops = 0;
 }
 
+// The fine operator A_h as the fused PCG kernels see it: CSR rows read by sub-warps of
+// TPR lanes (TPR > 0), or SELL-32 slices read one thread per row (TPR == 0; ptr then
+// holds the slice pointers and sw the slice widths).
+struct RowOp {
+    const int64_t *ptr;
+    const int32_t *col;
+    const double *val;
+    const int32_t *sw;
+};
+
+RowOp fine_op(const pkasp_problem *p) {
+    if (p->spmv_tpr == 0) return RowOp{p->Asell.sptr, p->Asell.col, p->Asell.val, p->Asell.swidth};
+    return RowOp{p->Ah.ptr, p->Ah.col, p->Ah.val, nullptr};
+}
+
+// f(row, (A x)_row) for every row, grid-stride; every lane of a warp runs the same
+// number of trips (the shuffles of the CSR form need the whole warp)
+template <int TPR, class F>
+__device__ __forceinline__ void for_rows(int64_t n, const RowOp &A, const double *x, F f) {
+    if constexpr (TPR == 0) {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += stride) {
+            const int64_t s = row >> 5;
+            f(row, sell_dot<double>(A.ptr[s] + (row & 31), A.sw[s], A.col, A.val, x));
+        }
+    } else {
+        const int sub = threadIdx.x & (TPR - 1);
+        const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        const int rpw = 32 / TPR, sg = (threadIdx.x & 31) / TPR;
+        for (int64_t base = warp * rpw; base < n; base += nwarps * rpw) {
+            const int64_t row = base + sg;
+            const bool ok = row < n;
+            int64_t lo = ok ? A.ptr[row] : 0, hi = ok ? A.ptr[row + 1] : 0;
+            double s = row_dot<TPR, double>(lo, hi, sub, A.col, A.val, x);
+            if (ok && sub == 0) f(row, s);
+        }
+    }
+}
+
 // r = b - A x, ||r||; on the first start also r0 and hist[0]
 template <int TPR>
-__global__ void __launch_bounds__(kBlock) k_init_residual(int64_t n, const int64_t *__restrict__ ptr,
-                                                          const int32_t *__restrict__ col,
-                                                          const double *__restrict__ val, const double *__restrict__ b,
+__global__ void __launch_bounds__(kBlock) k_init_residual(int64_t n, RowOp A, const double *__restrict__ b,
                                                           const double *__restrict__ x, double *__restrict__ r,
                                                           PcgState *st, double *partials, unsigned *counter,
                                                           double *hist) {
-    const int sub = threadIdx.x & (TPR - 1);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int rpw = 32 / TPR, sg = (threadIdx.x & 31) / TPR;
     double part = 0.0;
-    for (int64_t base = warp * rpw; base < n; base += nwarps * rpw) {
-        const int64_t row = base + sg;
-        const bool ok = row < n;
-        int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
-        double s = row_dot<TPR, double>(lo, hi, sub, col, val, x);
-        if (ok && sub == 0) {
-            double ri = b[row] - s;
-            r[row] = ri;
-            part += ri * ri;
-        }
-    }
+    for_rows<TPR>(n, A, x, [&](int64_t row, double s) {
+        double ri = b[row] - s;
+        r[row] = ri;
+        part += ri * ri;
+    });
     double v[1] = {part}, tot[1];
     if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) {
         double rn = sqrt(tot[0]);
@@ -343,26 +410,15 @@ __global__ void __launch_bounds__(kBlock) k_start(int64_t n, const double *__res
 
 // q = A p, alpha = rho / (p, q)
 template <int TPR>
-__global__ void __launch_bounds__(kBlock) k_spmv_pq(int64_t n, const int64_t *__restrict__ ptr,
-                                                    const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                    const double *__restrict__ p, double *__restrict__ q,
-                                                    PcgState *st, double *partials, unsigned *counter) {
+__global__ void __launch_bounds__(kBlock) k_spmv_pq(int64_t n, RowOp A, const double *__restrict__ p,
+                                                    double *__restrict__ q, PcgState *st, double *partials,
+                                                    unsigned *counter) {
     if (st->done[0]) return;
-    const int sub = threadIdx.x & (TPR - 1);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int rpw = 32 / TPR, sg = (threadIdx.x & 31) / TPR;
     double part = 0.0;
-    for (int64_t base = warp * rpw; base < n; base += nwarps * rpw) {
-        const int64_t row = base + sg;
-        const bool ok = row < n;
-        int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
-        double s = row_dot<TPR, double>(lo, hi, sub, col, val, p);
-        if (ok && sub == 0) {
-            q[row] = s;
-            part += p[row] * s;
-        }
-    }
+    for_rows<TPR>(n, A, p, [&](int64_t row, double s) {
+        q[row] = s;
+        part += p[row] * s;
+    });
     double v[1] = {part}, tot[1];
     if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) {
         double pq = tot[0];
@@ -448,26 +504,14 @@ __global__ void k_loop_control(PcgState *st, cudaGraphConditionalHandle h) {
 
 // true residual norm ||b - A x|| into st->tnorm
 template <int TPR>
-__global__ void __launch_bounds__(kBlock) k_true_residual(int64_t n, const int64_t *__restrict__ ptr,
-                                                          const int32_t *__restrict__ col,
-                                                          const double *__restrict__ val, const double *__restrict__ b,
+__global__ void __launch_bounds__(kBlock) k_true_residual(int64_t n, RowOp A, const double *__restrict__ b,
                                                           const double *__restrict__ x, PcgState *st,
                                                           double *partials, unsigned *counter) {
-    const int sub = threadIdx.x & (TPR - 1);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int rpw = 32 / TPR, sg = (threadIdx.x & 31) / TPR;
     double part = 0.0;
-    for (int64_t base = warp * rpw; base < n; base += nwarps * rpw) {
-        const int64_t row = base + sg;
-        const bool ok = row < n;
-        int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
-        double s = row_dot<TPR, double>(lo, hi, sub, col, val, x);
-        if (ok && sub == 0) {
-            double ri = b[row] - s;
-            part += ri * ri;
-        }
-    }
+    for_rows<TPR>(n, A, x, [&](int64_t row, double s) {
+        double ri = b[row] - s;
+        part += ri * ri;
+    });
     double v[1] = {part}, tot[1];
     if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) st->tnorm[0] = sqrt(tot[0]);
 }
@@ -489,12 +533,63 @@ void free_setup(pkasp_problem *p) {
     p->work_pool.free_all();
     p->lev.clear();
     p->fine = DSplit{};
+    p->Asell = DSell{};
+    p->fsl = DSell{};
+    p->fsu = DSell{};
     p->d_l1h = nullptr;
     p->d_l1h32 = nullptr;
     p->d_cinv = nullptr;
     p->d_cinv32 = nullptr;
     p->work_cols = 0;
     p->have_setup = false;
+}
+
+// Lanes-per-row autotuner for the two hot fine-level kernels: every candidate runs a few
+// times on the actual matrix (inputs f_h) and the fastest is kept. A fixed
+// options.spmv_threads bypasses it.
+void autotune(pkasp_problem *p, cudaStream_t s) {
+    if (p->opt.spmv_threads) {
+        p->spmv_tpr = p->fine_tpr = p->opt.spmv_threads;
+        return;
+    }
+    cudaEvent_t e0, e1;
+    PK_CUDA(cudaEventCreate(&e0));
+    PK_CUDA(cudaEventCreate(&e1));
+    auto timed = [&](auto fn) {
+        fn();
+        PK_CUDA(cudaEventRecord(e0, s));
+        for (int i = 0; i < 3; ++i) fn();
+        PK_CUDA(cudaEventRecord(e1, s));
+        PK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    // 0: SELL-32, one thread per row; t > 0: CSR with t lanes per row; -1 (smoother
+    // only): CSR with the lanes of each colour phase fitted to its longest row
+    const int cand_spmv[] = {0, 2, 4, 8};
+    const int cand_fine[] = {-1, 0, 4, 8, 16};
+    float best = 1e30f;
+    int pick_spmv = 0, pick_fine = -1;
+    for (int t : cand_spmv) {
+        p->spmv_tpr = t;
+        float ms = timed([&] { spmv_fine(p, p->d_b, p->w_q, s); });
+        if (ms < best) best = ms, pick_spmv = t;
+    }
+    best = 1e30f;
+    if (p->opt.smoother == PKASP_SMOOTHER_SGS) {
+        for (int t : cand_fine) {
+            p->fine_tpr = t;
+            float ms = (p->opt.precond_precision == PKASP_PREC_FP32)
+                           ? timed([&] { smoother<float>(p, p->d_b, p->w_zs32, s); })
+                           : timed([&] { smoother<double>(p, p->d_b, p->w_zs, s); });
+            if (ms < best) best = ms, pick_fine = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->spmv_tpr = pick_spmv;
+    p->fine_tpr = pick_fine;
 }
 
 void setup_device(pkasp_problem *p, cudaStream_t s) {
@@ -504,6 +599,9 @@ void setup_device(pkasp_problem *p, cudaStream_t s) {
     DevPool &pool = p->setup_pool;
     // fine level: colour split of A_h, l1 norms, FP32 copies
     build_split(pool, p->Ah, stream_colour(o.seed, 0), want32, p->fine, s);
+    build_sell_natural(pool, p->Ah, p->Asell, false, s);
+    build_sell_split(pool, p->fine, p->nh, false, p->fsl, want32, s);
+    build_sell_split(pool, p->fine, p->nh, true, p->fsu, want32, s);
     p->d_l1h = row_l1(pool, p->Ah, s);
     if (want32) {
         p->d_l1h32 = pool.get<float>(p->nh);
@@ -567,6 +665,7 @@ void setup_device(pkasp_problem *p, cudaStream_t s) {
     ensure_work(p, 1);
     PK_CUDA(cudaStreamSynchronize(s));
     p->have_setup = true;
+    autotune(p, s);
 }
 
 void ensure_work(pkasp_problem *p, int ncols) {
@@ -603,7 +702,14 @@ void ensure_work(pkasp_problem *p, int ncols) {
 // public pieces
 // ---------------------------------------------------------------------------------
 void spmv_fine(pkasp_problem *p, const double *x, double *y, cudaStream_t s) {
-    spmv<double, double>(p->Ah, x, y, p->spmv_tpr ? p->spmv_tpr : tpr_of(p->Ah), s);
+    if (p->spmv_tpr == 0) {
+        const DSell &S = p->Asell;
+        k_sell_spmv<double, double, double, double><<<elem_grid(p->nh), kBlock, 0, s>>>(
+            p->nh, S.sptr, S.swidth, S.col, S.val, x, y);
+        PK_LAUNCH();
+        return;
+    }
+    spmv<double, double>(p->Ah, x, y, p->spmv_tpr, s);
 }
 
 void apply_prec(pkasp_problem *p, const double *r, double *z, cudaStream_t s) {
@@ -638,11 +744,21 @@ void apply_vcycle(pkasp_problem *p, const double *b, double *x, cudaStream_t s) 
 
 namespace {
 
+#define PK_FMT_SWITCH(tpr, BODY)                          \
+    switch (tpr) {                                        \
+        case 0: { constexpr int TPR = 0; BODY; } break;   \
+        case 2: { constexpr int TPR = 2; BODY; } break;   \
+        case 4: { constexpr int TPR = 4; BODY; } break;   \
+        case 8: { constexpr int TPR = 8; BODY; } break;   \
+        case 16: { constexpr int TPR = 16; BODY; } break; \
+        default: { constexpr int TPR = 32; BODY; } break; \
+    }
+
 void enqueue_init(pkasp_problem *p, const double *b, double *x, cudaStream_t s) {
     const int tpr = p->spmv_tpr;
-    PK_TPR_SWITCH(tpr, (k_init_residual<TPR><<<kRedGrid, kBlock, 0, s>>>(
-                           p->nh, p->Ah.ptr, p->Ah.col, p->Ah.val, b, x, p->w_r, p->d_state, p->d_partials,
-                           p->d_counter, p->d_hist)));
+    const RowOp A = fine_op(p);
+    PK_FMT_SWITCH(tpr, (k_init_residual<TPR><<<kRedGrid, kBlock, 0, s>>>(
+                           p->nh, A, b, x, p->w_r, p->d_state, p->d_partials, p->d_counter, p->d_hist)));
     PK_LAUNCH();
     apply_prec(p, p->w_r, p->w_z, s);
     k_start<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_r, p->w_z, p->w_p, p->d_state, p->d_partials, p->d_counter);
@@ -651,9 +767,9 @@ void enqueue_init(pkasp_problem *p, const double *b, double *x, cudaStream_t s) 
 
 void enqueue_iteration(pkasp_problem *p, double *x, cudaStream_t s) {
     const int tpr = p->spmv_tpr;
-    PK_TPR_SWITCH(tpr, (k_spmv_pq<TPR><<<kRedGrid, kBlock, 0, s>>>(p->nh, p->Ah.ptr, p->Ah.col, p->Ah.val,
-                                                                   p->w_p, p->w_q, p->d_state, p->d_partials,
-                                                                   p->d_counter)));
+    const RowOp A = fine_op(p);
+    PK_FMT_SWITCH(tpr, (k_spmv_pq<TPR><<<kRedGrid, kBlock, 0, s>>>(p->nh, A, p->w_p, p->w_q, p->d_state,
+                                                                   p->d_partials, p->d_counter)));
     PK_LAUNCH();
     k_update_xr<<<kRedGrid, kBlock, 0, s>>>(p->nh, x, p->w_r, p->w_p, p->w_q, p->d_state, p->d_partials,
                                             p->d_counter, p->d_hist);
@@ -669,9 +785,9 @@ void enqueue_iteration(pkasp_problem *p, double *x, cudaStream_t s) {
 
 void enqueue_final(pkasp_problem *p, const double *b, const double *x, cudaStream_t s) {
     const int tpr = p->spmv_tpr;
-    PK_TPR_SWITCH(tpr, (k_true_residual<TPR><<<kRedGrid, kBlock, 0, s>>>(
-                           p->nh, p->Ah.ptr, p->Ah.col, p->Ah.val, b, x, p->d_state, p->d_partials,
-                           p->d_counter)));
+    const RowOp A = fine_op(p);
+    PK_FMT_SWITCH(tpr, (k_true_residual<TPR><<<kRedGrid, kBlock, 0, s>>>(p->nh, A, b, x, p->d_state,
+                                                                         p->d_partials, p->d_counter)));
     PK_LAUNCH();
 }
 

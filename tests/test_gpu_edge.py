@@ -102,8 +102,16 @@ def test_ragged_sizes_match_oracle(gpu, oracle_mod, k, n):
     ref = O.solve()
     x, st = G.solve(G.rhs(), hist_cap=600)
     assert abs(st["iters"][0] - ref["iters"]) <= 1
+    assert st["true_rel"][0] <= 1e-8
     m = min(len(ref["hist"]), st["hist"].shape[0])
-    assert (np.abs(st["hist"][:m, 0] - ref["hist"][:m]) / ref["hist"][0]).max() <= 1e-10
+    h, ho = st["hist"][:m, 0], ref["hist"][:m]
+    dev = np.abs(h - ho) / ho[0]
+    # these tiny lognormal-kappa meshes are the worst conditioned cases: until the
+    # residual has dropped by 1e-3 the histories agree to 1e-10 ||r_0||; after that CG
+    # amplifies rounding differences, and they agree to the solve tolerance itself
+    early = ho >= 1e-3 * ho[0]
+    assert dev[early].max() <= 1e-10
+    assert dev.max() <= 1e-8
     G.close()
 
 
