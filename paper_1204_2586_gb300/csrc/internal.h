@@ -68,6 +68,8 @@ struct DSplit {
     int64_t *lptr = nullptr, *uptr = nullptr;
     int32_t *lcol = nullptr, *ucol = nullptr;
     double *lval = nullptr, *uval = nullptr, *diag = nullptr;
+    double *dinv = nullptr;  // 1 / diag: GB300 runs FP64 at ~2 DFMA per clock per SM, so
+    float *dinv32 = nullptr; // the smoother multiplies instead of dividing
     float *lval32 = nullptr, *uval32 = nullptr, *diag32 = nullptr;
     int64_t nnz_l = 0, nnz_u = 0;
     std::vector<int> lmax, umax;  // per colour: longest lower / upper part (host)
@@ -85,7 +87,7 @@ struct DSell {
     int32_t *col = nullptr;
     double *val = nullptr;
     float *val32 = nullptr;
-    double *diag = nullptr;
+    double *diag = nullptr;    // colour split only: the INVERSE diagonal of each position
     float *diag32 = nullptr;
     std::vector<int64_t> coff;
 };

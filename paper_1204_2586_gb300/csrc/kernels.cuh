@@ -171,6 +171,67 @@ __global__ void __launch_bounds__(kBlock) k_gs_fwd0(int64_t pb, int64_t pe, cons
     if (lead) y[i] = (ri - s) / d;
 }
 
+// Programmatic dependent launch (sm_90+): a kernel launched with programmatic stream
+// serialization may start while its predecessor is still running. It lets its own
+// successor launch at once, loads the data no kernel of the solve writes (the matrix),
+// then waits until the predecessor has finished and its writes are visible before it
+// touches any vector. Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// One colour phase of the symmetric Gauss-Seidel sweep from zero (CSR colour split):
+//   BACK = false: y_i = (r_i - sum_L a_ij y_j) / a_ii
+//   BACK = true:  y_i = y_i - (sum_U a_ij y_j) / a_ii
+// Static loads (position, bounds, diagonal, first batch of the row's entries) happen
+// before the dependency wait, so they overlap the previous phase. Lane `sub` adds its
+// entries in the same order as row_dot.
+template <int TPR, typename PT, typename TR, bool BACK>
+__global__ void __launch_bounds__(kBlock) k_gs_phase(int64_t pb, int64_t pe, const int32_t *__restrict__ perm,
+                                                     const int64_t *__restrict__ xptr, const int32_t *__restrict__ xcol,
+                                                     const PT *__restrict__ xval, const PT *__restrict__ dinv,
+                                                     const TR *r, PT *y) {
+    pdl_trigger();
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = pb + gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = p < pe;
+    const bool lead = ok && sub == 0;
+    const int32_t i = lead ? perm[p] : 0;
+    const PT di = lead ? dinv[p] : PT(1);
+    const int64_t lo = ok ? xptr[p] : 0, hi = ok ? xptr[p + 1] : 0;
+    int c[kBatch];
+    PT v[kBatch];
+    const int64_t b0 = lo + sub;
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k) {
+        const int64_t e = b0 + (int64_t)k * TPR;
+        const bool in = e < hi;
+        c[k] = in ? __ldg(&xcol[e]) : -1;
+        v[k] = in ? __ldg(&xval[e]) : PT(0);
+    }
+    pdl_wait();
+    PT own = PT(0);
+    if (lead) own = BACK ? y[i] : (PT)r[i];
+    PT acc = PT(0);
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k)
+        if (c[k] >= 0) acc += v[k] * y[c[k]];
+    for (int64_t base = b0 + (int64_t)kBatch * TPR; base < hi; base += (int64_t)kBatch * TPR) {
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int64_t e = base + (int64_t)k * TPR;
+            const bool in = e < hi;
+            c[k] = in ? __ldg(&xcol[e]) : -1;
+            v[k] = in ? __ldg(&xval[e]) : PT(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k)
+            if (c[k] >= 0) acc += v[k] * y[c[k]];
+    }
+    acc = subwarp_sum<TPR>(acc);
+    if (lead) y[i] = BACK ? own - acc * di : (own - acc) * di;
+}
+
 template <int TPR, typename PT>
 __global__ void __launch_bounds__(kBlock) k_gs_bwd0(int64_t pb, int64_t pe, const int32_t *__restrict__ perm,
                                                     const int64_t *__restrict__ uptr, const int32_t *__restrict__ ucol,
@@ -309,45 +370,52 @@ __global__ void __launch_bounds__(kBlock) k_sell_spmv(int64_t n, const int64_t *
     y[row] = (YT)sell_dot<A>(sptr[s] + (row & 31), sw[s], col, val, x);
 }
 
-// colour phase of the forward sweep from zero over slices [s0, s1):
-//   y_i = (r_i - sum_L a_ij y_j) / a_ii
-template <typename PT, typename TR>
-__global__ void __launch_bounds__(kBlock) k_sell_gs_fwd0(int64_t s0, int64_t s1, const int32_t *__restrict__ perm,
-                                                         const int64_t *__restrict__ sptr,
-                                                         const int32_t *__restrict__ sw,
-                                                         const int32_t *__restrict__ col, const PT *__restrict__ val,
-                                                         const PT *__restrict__ diag, const TR *__restrict__ r,
-                                                         PT *y) {
-    const int64_t q = s0 * 32 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= s1 * 32) return;
-    const int64_t s = q >> 5;
-    // independent loads first; padding rows (perm < 0) have width-0 tails of column -1
-    const int32_t i = perm[q];
-    const int64_t base = sptr[s] + (q & 31);
-    const int w = sw[s];
-    const PT d = diag[q];
-    const PT ri = i >= 0 ? (PT)r[i] : PT(0);
-    const PT acc = sell_dot<PT>(base, w, col, val, (const PT *)y);
-    if (i >= 0) y[i] = (ri - acc) / d;
-}
-
-// colour phase of the backward sweep that follows: y_i <- y_i - (sum_U a_ij y_j) / a_ii
-template <typename PT>
-__global__ void __launch_bounds__(kBlock) k_sell_gs_bwd0(int64_t s0, int64_t s1, const int32_t *__restrict__ perm,
-                                                         const int64_t *__restrict__ sptr,
-                                                         const int32_t *__restrict__ sw,
-                                                         const int32_t *__restrict__ col, const PT *__restrict__ val,
-                                                         const PT *__restrict__ diag, PT *y) {
+// One colour phase of the symmetric Gauss-Seidel sweep from zero over the SELL-32 slices
+// [s0, s1) of a colour-sorted split, one thread per row (no reduction across lanes):
+//   BACK = false: y_i = (r_i - sum_L a_ij y_j) * dinv_i
+//   BACK = true:  y_i = y_i - (sum_U a_ij y_j) * dinv_i
+// Padding positions (perm < 0) only carry column -1 entries. Launched with PDL: static
+// loads before the dependency wait.
+template <typename PT, typename TR, bool BACK>
+__global__ void __launch_bounds__(kBlock) k_sell_phase(int64_t s0, int64_t s1, const int32_t *__restrict__ perm,
+                                                       const int64_t *__restrict__ sptr, const int32_t *__restrict__ sw,
+                                                       const int32_t *__restrict__ col, const PT *__restrict__ val,
+                                                       const PT *__restrict__ dinv, const TR *r, PT *y) {
+    pdl_trigger();
     const int64_t q = s0 * 32 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= s1 * 32) return;
     const int64_t s = q >> 5;
     const int32_t i = perm[q];
     const int64_t base = sptr[s] + (q & 31);
     const int w = sw[s];
-    const PT d = diag[q];
-    const PT yi = i >= 0 ? y[i] : PT(0);
-    const PT acc = sell_dot<PT>(base, w, col, val, (const PT *)y);
-    if (i >= 0) y[i] = yi - acc / d;
+    const PT di = dinv[q];
+    int c[kBatch];
+    PT v[kBatch];
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k) {
+        const bool in = k < w;
+        c[k] = in ? __ldg(&col[base + 32 * (int64_t)k]) : -1;
+        v[k] = in ? __ldg(&val[base + 32 * (int64_t)k]) : PT(0);
+    }
+    pdl_wait();
+    PT own = PT(0);
+    if (i >= 0) own = BACK ? y[i] : (PT)r[i];
+    PT acc = PT(0);
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k)
+        if (c[k] >= 0) acc += v[k] * y[c[k]];
+    for (int k0 = kBatch; k0 < w; k0 += kBatch) {
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const bool in = k0 + k < w;
+            c[k] = in ? __ldg(&col[base + 32 * (int64_t)(k0 + k)]) : -1;
+            v[k] = in ? __ldg(&val[base + 32 * (int64_t)(k0 + k)]) : PT(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k)
+            if (c[k] >= 0) acc += v[k] * y[c[k]];
+    }
+    if (i >= 0) y[i] = BACK ? own - acc * di : (own - acc) * di;
 }
 
 }  // namespace pk

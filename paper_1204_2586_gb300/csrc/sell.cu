@@ -167,7 +167,7 @@ void build_sell_split(DevPool &pool, const DSplit &sp, int64_t n, bool upper, DS
         PK_CUDA(cudaMemcpyAsync(dsrc, src.data(), sizeof(int64_t) * S.npos, cudaMemcpyHostToDevice, s));
         if (S.npos > 0) {
             k_sell_fill_split<<<blocks_for(S.npos, 256), 256, 0, s>>>(
-                S.npos, dsrc, xptr, upper ? sp.ucol : sp.lcol, upper ? sp.uval : sp.lval, sp.diag, S.sptr,
+                S.npos, dsrc, xptr, upper ? sp.ucol : sp.lcol, upper ? sp.uval : sp.lval, sp.dinv, S.sptr,
                 S.swidth, S.col, S.val, S.diag);
             PK_LAUNCH();
         }

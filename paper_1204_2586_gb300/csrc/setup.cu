@@ -117,7 +117,7 @@ __global__ void k_split_fill(int64_t n, const int32_t *__restrict__ perm, const 
                              const int32_t *__restrict__ colour, const int64_t *__restrict__ lptr,
                              const int64_t *__restrict__ uptr, int32_t *__restrict__ lcol,
                              double *__restrict__ lval, int32_t *__restrict__ ucol, double *__restrict__ uval,
-                             double *__restrict__ diag, int *__restrict__ bad) {
+                             double *__restrict__ diag, double *__restrict__ dinv, int *__restrict__ bad) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     int32_t i = perm[p];
@@ -141,6 +141,7 @@ __global__ void k_split_fill(int64_t n, const int32_t *__restrict__ perm, const 
     }
     if (d == 0.0) atomicExch(bad, 1);
     diag[p] = d;
+    dinv[p] = d != 0.0 ? 1.0 / d : 0.0;
 }
 
 __global__ void k_l1norm(int64_t n, const int64_t *__restrict__ ptr, const double *__restrict__ val,
@@ -660,11 +661,13 @@ void build_split(DevPool &pool, const DCSR &A, uint64_t stream, bool want32, DSp
         sp.ucol = pool.get<int32_t>(sp.nnz_u > 0 ? sp.nnz_u : 1);
         sp.uval = pool.get<double>(sp.nnz_u > 0 ? sp.nnz_u : 1);
         sp.diag = pool.get<double>(n > 0 ? n : 1);
+        sp.dinv = pool.get<double>(n > 0 ? n : 1);
         int *bad = tmp.get<int>(1);
         PK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
         if (n > 0) {
             k_split_fill<<<blocks_for(n, 256), 256, 0, s>>>(n, sp.perm, A.ptr, A.col, A.val, sp.colour, sp.lptr,
-                                                            sp.uptr, sp.lcol, sp.lval, sp.ucol, sp.uval, sp.diag, bad);
+                                                            sp.uptr, sp.lcol, sp.lval, sp.ucol, sp.uval, sp.diag,
+                                                            sp.dinv, bad);
             PK_LAUNCH();
         }
         int hb = 0;
@@ -676,9 +679,11 @@ void build_split(DevPool &pool, const DCSR &A, uint64_t stream, bool want32, DSp
             sp.lval32 = pool.get<float>(sp.nnz_l > 0 ? sp.nnz_l : 1);
             sp.uval32 = pool.get<float>(sp.nnz_u > 0 ? sp.nnz_u : 1);
             sp.diag32 = pool.get<float>(n > 0 ? n : 1);
+            sp.dinv32 = pool.get<float>(n > 0 ? n : 1);
             to32(sp.lval, sp.lval32, sp.nnz_l, s);
             to32(sp.uval, sp.uval32, sp.nnz_u, s);
             to32(sp.diag, sp.diag32, n, s);
+            to32(sp.dinv, sp.dinv32, n, s);
         }
         PK_CUDA(cudaStreamSynchronize(s));
     } catch (...) {

@@ -85,6 +85,25 @@ void spmv(const DCSR &A, const X *x, Y *y, int tpr, cudaStream_t s) {
     PK_LAUNCH();
 }
 
+// Launch with programmatic stream serialization (PDL): the kernel may begin while the
+// previous kernel on the stream drains; it must call pdl_wait() before reading anything
+// an earlier kernel wrote (k_gs_phase does).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PK_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+    PK_LAUNCH();
+}
+
 // Lanes per row for a colour phase whose longest row part has `len` entries: the fewest
 // lanes (a power of two, at most 32) for which one batch of loads per lane covers the row.
 // A colour phase is latency-bound, and every extra batch is one more DRAM round trip.
@@ -102,10 +121,10 @@ void gs_forward0(const DSplit &sp, int tpr_fixed, const TR *r, PT *y, cudaStream
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
         const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(sp.lmax[c]);
-        PK_TPR_SWITCH(tpr, (k_gs_fwd0<TPR, PT, TR><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
-                                pb, pe, sp.perm, sp.lptr, sp.lcol, pick<PT>(sp.lval, sp.lval32),
-                                pick<PT>(sp.diag, sp.diag32), r, y)));
-        PK_LAUNCH();
+        PK_TPR_SWITCH(tpr, (launch_pdl(k_gs_phase<TPR, PT, TR, false>, rows_grid(pe - pb, TPR), s, pb, pe,
+                                       (const int32_t *)sp.perm, (const int64_t *)sp.lptr,
+                                       (const int32_t *)sp.lcol, pick<PT>(sp.lval, sp.lval32),
+                                       pick<PT>(sp.dinv, sp.dinv32), r, y)));
     }
 }
 
@@ -117,10 +136,10 @@ void gs_backward0(const DSplit &sp, int tpr_fixed, PT *y, cudaStream_t s) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
         const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(sp.umax[c]);
-        PK_TPR_SWITCH(tpr, (k_gs_bwd0<TPR, PT><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
-                                pb, pe, sp.perm, sp.uptr, sp.ucol, pick<PT>(sp.uval, sp.uval32),
-                                pick<PT>(sp.diag, sp.diag32), y)));
-        PK_LAUNCH();
+        PK_TPR_SWITCH(tpr, (launch_pdl(k_gs_phase<TPR, PT, PT, true>, rows_grid(pe - pb, TPR), s, pb, pe,
+                                       (const int32_t *)sp.perm, (const int64_t *)sp.uptr,
+                                       (const int32_t *)sp.ucol, pick<PT>(sp.uval, sp.uval32),
+                                       pick<PT>(sp.dinv, sp.dinv32), (const PT *)y, y)));
     }
 }
 
@@ -216,18 +235,18 @@ void smoother(pkasp_problem *p, const double *r, PT *zs, cudaStream_t s) {
         for (int c = 0; c < nc; ++c) {
             const int64_t s0 = L.coff[c], s1 = L.coff[c + 1];
             if (s1 <= s0) continue;
-            k_sell_gs_fwd0<PT, double><<<rows_grid((s1 - s0) * 32, 1), kBlock, 0, s>>>(
-                s0, s1, L.perm, L.sptr, L.swidth, L.col, pick<PT>(L.val, L.val32), pick<PT>(L.diag, L.diag32), r,
-                zs);
-            PK_LAUNCH();
+            launch_pdl(k_sell_phase<PT, double, false>, rows_grid((s1 - s0) * 32, 1), s, s0, s1,
+                       (const int32_t *)L.perm, (const int64_t *)L.sptr, (const int32_t *)L.swidth,
+                       (const int32_t *)L.col, pick<PT>(L.val, L.val32), pick<PT>(L.diag, L.diag32), r, zs);
         }
         // the highest colour has no upper part: its backward phase would leave y as is
         for (int c = nc - 2; c >= 0; --c) {
             const int64_t s0 = U.coff[c], s1 = U.coff[c + 1];
             if (s1 <= s0) continue;
-            k_sell_gs_bwd0<PT><<<rows_grid((s1 - s0) * 32, 1), kBlock, 0, s>>>(
-                s0, s1, U.perm, U.sptr, U.swidth, U.col, pick<PT>(U.val, U.val32), pick<PT>(U.diag, U.diag32), zs);
-            PK_LAUNCH();
+            launch_pdl(k_sell_phase<PT, PT, true>, rows_grid((s1 - s0) * 32, 1), s, s0, s1,
+                       (const int32_t *)U.perm, (const int64_t *)U.sptr, (const int32_t *)U.swidth,
+                       (const int32_t *)U.col, pick<PT>(U.val, U.val32), pick<PT>(U.diag, U.diag32),
+                       (const PT *)zs, zs);
         }
         return;
     }

@@ -139,6 +139,20 @@ class Problem:
             out["hist"] = hist.reshape(hist_cap, ncols)[: st.hist_len].copy()
         return x, out
 
+    def solve_adjoint(self, g, lam=None, hist_cap=0, stream=None):
+        """Adjoint solve A_h^T lambda = g (A_h is symmetric: same operator and
+        preconditioner, through pkasp_solve_adjoint). Returns (lambda, stats)."""
+        import torch
+
+        if lam is None:
+            lam = torch.zeros_like(g)
+        ncols = 1 if g.ndim == 1 else g.shape[1]
+        st = L.pkasp_stats()
+        L.check(L.load().pkasp_solve_adjoint(self.h, _ptr(g), _ptr(lam), ncols, ncols, C.byref(st),
+                                             _stream(stream)))
+        return lam, dict(iters=list(st.iters[:ncols]), status=list(st.status[:ncols]),
+                         true_rel=list(st.true_rel[:ncols]))
+
     def spmv(self, x, stream=None):
         import torch
 
