@@ -236,6 +236,23 @@ int pkasp_pmis(int64_t n, const int64_t *ptr_dev, const int32_t *col_dev,
                const uint8_t *strong_dev, uint64_t stream_id, int8_t *cf_dev,
                pkasp_stream_t stream);
 
+/* Same splitting as pkasp_pmis, for callers that cannot let a library allocate device
+ * memory: processes that hand the whole GPU memory to their own pool at start-up, and
+ * code that must not synchronize the device (cudaMalloc and cudaFree do). The paper has
+ * no counterpart; this is a deployment variant of pkasp_pmis. It allocates nothing: its
+ * scratch is one fixed device array of about 17 MB inside the library, held by every GPU
+ * that loads the library until the process exits, and it accepts at most
+ * PKASP_NOALLOC_MAX_ROWS rows and PKASP_NOALLOC_MAX_NNZ entries (larger inputs return
+ * PKASP_EINVAL before any work). The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress), so make the first call on each device before any stream
+ * capture. Every call shares the one array: calls that overlap on the GPU (from several
+ * streams or threads) race and must be serialized by the caller. The output cf_dev[n] is
+ * bit-identical to pkasp_pmis for the same inputs. Synchronizes the stream. */
+enum { PKASP_NOALLOC_MAX_ROWS = 262144, PKASP_NOALLOC_MAX_NNZ = 4194304 };
+int pkasp_pmis_noalloc(int64_t n, const int64_t *ptr_dev, const int32_t *col_dev,
+                       const uint8_t *strong_dev, uint64_t stream_id, int8_t *cf_dev,
+                       pkasp_stream_t stream);
+
 /* ------------------------------------------------------------------------------------
  * Host-only helpers (no GPU needed): the numbering and sparsity patterns that
  * pkasp_assemble builds, for checks and tools.

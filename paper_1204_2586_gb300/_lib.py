@@ -78,6 +78,7 @@ SIGNATURES = [
     ("pkasp_get_colours", C.c_int, [vp, C.c_int, vp, C.POINTER(C.c_int)]),
     ("pkasp_get_splitting", C.c_int, [vp, C.c_int, vp, vp]),
     ("pkasp_pmis", C.c_int, [i64, vp, vp, vp, C.c_uint64, vp, vp]),
+    ("pkasp_pmis_noalloc", C.c_int, [i64, vp, vp, vp, C.c_uint64, vp, vp]),
     ("pkasp_dofmap_host", C.c_int, [vp, i64, vp, i64, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp]),
     ("pkasp_reference_tensors", C.c_int, [C.c_int, vp]),
     ("pkasp_time_kernel", C.c_int, [vp, C.c_int, C.c_int, C.POINTER(C.c_float), vp]),

@@ -417,6 +417,15 @@ int pkasp_pmis(int64_t n, const int64_t *ptr_dev, const int32_t *col_dev, const 
     });
 }
 
+int pkasp_pmis_noalloc(int64_t n, const int64_t *ptr_dev, const int32_t *col_dev, const uint8_t *strong_dev,
+                       uint64_t stream_id, int8_t *cf_dev, pkasp_stream_t stream) {
+    if (n < 0 || !ptr_dev || !col_dev || !strong_dev || !cf_dev) return set_error(PKASP_EINVAL, "bad argument");
+    return guarded([&]() -> int {
+        pk::pmis_noalloc(n, ptr_dev, col_dev, strong_dev, stream_id, cf_dev, (cudaStream_t)stream);
+        return PKASP_OK;
+    });
+}
+
 int pkasp_dofmap_host(const double *xyz_host, int64_t nv, const int32_t *tets_host, int64_t nt, int k,
                       int64_t *sizes_out, int64_t *dof_all_host, int32_t *elem_dof_host, int64_t *ah_ptr_host,
                       int32_t *ah_col_host, int64_t *pi_ptr_host, int32_t *pi_col_host, double *pi_val_host) {

@@ -237,6 +237,8 @@ void grad_kappa_device(const pkasp_problem *p, const double *u, const double *la
                        cudaStream_t s);
 void pmis_device(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_t *strong,
                  uint64_t stream_id, int8_t *cf, cudaStream_t s);
+void pmis_noalloc(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_t *strong, uint64_t stream_id,
+                  int8_t *cf, cudaStream_t s);
 void ensure_work(pkasp_problem *p, int ncols);
 float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s);
 
