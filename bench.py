@@ -32,7 +32,7 @@ UNIT = "MDOF*iter/s"
 CONFIG = {
     "workload": "P3 Poisson, kappa=1, 32^3 jittered Kuhn cubes (196,608 tets, 857,375 unknowns), "
                 "sine source, FP64, PCG to rel. residual 1e-8, additive aux-space preconditioner "
-                "(1 SGS sweep + 1 P1 AMG V-cycle, PMIS + ext+i, theta=0.25)",
+                "(1 SGS sweep + 1 P1 AMG V-cycle, PMIS + ext+i, theta=0.25, l1-Jacobi level smoothing)",
     "mesh": "unit cube, 32^3 cubes x 6 Kuhn tets, interior vertices jittered by <=0.2h (seed 0)",
     "k": 3,
     "n_h": 857375,
@@ -40,6 +40,9 @@ CONFIG = {
     "parallelism": "replicas (one independent solve per GPU)",
 }
 ORACLE_SAMPLE_ITERS = 12
+# AMG level smoother: l1-Jacobi (1), one kernel per smoothing step; multicolour GS on the
+# dense coarse levels needs one launch per colour and costs ~25x more per V-cycle here
+LEVEL_SMOOTHER = 1
 
 
 def peaks():
@@ -121,7 +124,7 @@ def run_cpu_oracle(steps, warmup, sample_iters=ORACLE_SAMPLE_ITERS):
 
     xyz, t = kuhn_mesh(WORKLOAD["n"], WORKLOAD["jitter"], WORKLOAD["mesh_seed"])
     P = oracle.Problem(xyz, t, WORKLOAD["k"])
-    P.setup(theta=0.25, max_iter=sample_iters)
+    P.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, max_iter=sample_iters)
     times, iters = [], []
     for i in range(warmup + steps):
         t0 = time.perf_counter()
@@ -185,7 +188,7 @@ def main():
     torch.cuda.synchronize()
     assemble_s = time.perf_counter() - t_as
     t_su = time.perf_counter()
-    G.setup(theta=0.25, use_graph=0 if args.eager else 1)
+    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, use_graph=0 if args.eager else 1)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_su
     b = G.rhs()
@@ -261,12 +264,29 @@ def main():
     # one symmetric GS application from zero reads each off-diagonal entry once (value +
     # column) and per row: diagonal, r, y (write, then read-modify-write), lptr/uptr, perm
     smoother_bytes = 12 * (nnz - nh) + 52 * nh
+    info64 = G.info
+    # the mixed-precision variant of the same solve: FP32 smoother / I_P / AMG, FP64 flexible CG
+    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, precond_precision=1, use_graph=0 if args.eager else 1)
+    for _ in range(2):
+        st32 = step()
+    ms32 = []
+    for _ in range(3):
+        st32 = step()
+        ms32.append(st32["solve_ms"])
+    extra32 = {"fp32_precond_time_to_solution_s": min(ms32) / 1e3, "fp32_precond_iterations": st32["iters"][0],
+               "fp32_precond_true_rel_residual": st32["true_rel"][0],
+               "fp32_precond_speedup_vs_fp64": sol_s / (min(ms32) / 1e3)}
     extra = {"time_to_solution_s": sol_s, "iterations": iters[-1], "setup_s": setup_s,
-             "assemble_s": assemble_s, "levels": int(G.info.levels),
-             "level_rows": [int(v) for v in G.info.level_rows[: G.info.levels]],
-             "fine_colours": int(G.info.fine_colours), "op_complexity": G.info.op_complexity,
+             "assemble_s": assemble_s, "levels": int(info64.levels),
+             "level_rows": [int(v) for v in info64.level_rows[: info64.levels]],
+             "fine_colours": int(info64.fine_colours), "op_complexity": info64.op_complexity,
+             "spmv_layout": "SELL-32" if info64.spmv_layout == 0 else f"CSR x{info64.spmv_layout} lanes",
+             "smoother_layout": ("SELL-32" if info64.smoother_layout == 0 else
+                                 "CSR, lanes per colour" if info64.smoother_layout < 0 else
+                                 f"CSR x{info64.smoother_layout} lanes"),
              "smoother_ms": smoother_ms,
              "smoother_GBps": smoother_bytes / (smoother_ms / 1e3) / 1e9}
+    extra.update(extra32)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

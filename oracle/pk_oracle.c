@@ -944,13 +944,15 @@ void orc_problem_elem_dofs(const oproblem *P, int32_t *elem_dof) {
 
 /* ------------------------------------------------------------------------------------
  * 7. Multicolour ordering for the Gauss-Seidel smoothers (the paper's hybrid GS of
- *    Sec. 6.1 is replaced by a multicolour GS). Jones-Plassmann: vertex priority is
- *    (hash(stream, i), -i); each round every uncoloured vertex whose priority beats all
- *    its uncoloured neighbours takes the smallest colour not used by a neighbour
- *    coloured in an earlier round.
+ *    Sec. 6.1 is replaced by a multicolour GS). Jones-Plassmann with largest-degree-first
+ *    priorities: vertex priority is (degree, hash(stream, i), -i), the degree counting
+ *    the off-diagonal entries of the row; each round every uncoloured vertex whose
+ *    priority beats all its uncoloured neighbours takes the smallest colour not used by a
+ *    neighbour coloured in an earlier round.
  * ---------------------------------------------------------------------------------- */
-static int prio_beats(uint64_t hi, int64_t i, uint64_t hj, int64_t j) {
-    /* does vertex i beat vertex j? larger hash wins, then the lower index */
+static int prio_beats(int64_t di, uint64_t hi, int64_t i, int64_t dj, uint64_t hj, int64_t j) {
+    /* does vertex i beat vertex j? higher degree wins, then larger hash, then lower index */
+    if (di != dj) return di > dj;
     if (hi != hj) return hi > hj;
     return i < j;
 }
@@ -958,10 +960,13 @@ static int prio_beats(uint64_t hi, int64_t i, uint64_t hj, int64_t j) {
 int orc_colour_jp(int64_t n, const int64_t *ptr, const int32_t *col, uint64_t stream,
                   int32_t *colour) {
     uint64_t *h = (uint64_t *)xmalloc(sizeof(uint64_t) * (size_t)n);
+    int64_t *deg = (int64_t *)xmalloc(sizeof(int64_t) * (size_t)(n ? n : 1));
     uint8_t *pick = (uint8_t *)xmalloc((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         h[i] = sm64(stream, (uint64_t)i);
         colour[i] = -1;
+        deg[i] = 0;
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) deg[i] += (col[e] != i);
     }
     int64_t left = n;
     int ncol = 0;
@@ -973,7 +978,7 @@ int orc_colour_jp(int64_t n, const int64_t *ptr, const int32_t *col, uint64_t st
             for (int64_t e = ptr[i]; e < ptr[i + 1] && best; ++e) {
                 int64_t j = col[e];
                 if (j == i || colour[j] >= 0) continue;
-                if (!prio_beats(h[i], i, h[j], j)) best = 0;
+                if (!prio_beats(deg[i], h[i], i, deg[j], h[j], j)) best = 0;
             }
             pick[i] = (uint8_t)best;
         }
@@ -998,6 +1003,7 @@ int orc_colour_jp(int64_t n, const int64_t *ptr, const int32_t *col, uint64_t st
         }
     }
     free(pick);
+    free(deg);
     free(h);
     return ncol;
 }

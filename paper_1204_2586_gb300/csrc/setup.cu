@@ -54,13 +54,24 @@ __global__ void k_jp_pick(int64_t n, const int64_t *__restrict__ ptr, const int3
         pick[i] = 0;
         return;
     }
+    // largest-degree-first priority (degree, hash, -index); the degree counts the
+    // off-diagonal entries of the row (rows are sorted, so the diagonal appears once)
     const uint64_t hi = splitmix64(stream, (uint64_t)i);
+    const int64_t lo_i = ptr[i], hi_i = ptr[i + 1];
+    int64_t di = hi_i - lo_i;
+    for (int64_t e = lo_i; e < hi_i; ++e) di -= (col[e] == i);
     uint8_t best = 1;
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+    for (int64_t e = lo_i; e < hi_i; ++e) {
         int32_t j = col[e];
         if (j == i || colour[j] >= 0) continue;
-        uint64_t hj = splitmix64(stream, (uint64_t)j);
-        bool i_wins = (hi != hj) ? (hi > hj) : (i < j);
+        int64_t dj = ptr[j + 1] - ptr[j];
+        for (int64_t f = ptr[j]; f < ptr[j + 1]; ++f) dj -= (col[f] == j);
+        bool i_wins;
+        if (di != dj) i_wins = di > dj;
+        else {
+            uint64_t hj = splitmix64(stream, (uint64_t)j);
+            i_wins = (hi != hj) ? (hi > hj) : (i < j);
+        }
         if (!i_wins) {
             best = 0;
             break;

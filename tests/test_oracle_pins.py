@@ -209,13 +209,14 @@ def test_manufactured_solution_rate(oracle_mod, k):
 
 
 # ---------------------------------------------------------------------------------
-# Colouring: Jones-Plassmann with fixed priorities equals the sequential greedy
-# colouring in decreasing priority order.
+# Colouring: Jones-Plassmann with fixed priorities (degree, hash, -index) equals the
+# sequential greedy colouring in decreasing priority order.
 # ---------------------------------------------------------------------------------
 def _greedy_colouring(A, stream):
     n = A.shape[0]
     h = splitmix64(stream, np.arange(n))
-    order = sorted(range(n), key=lambda i: (-int(h[i]), i))
+    deg = [int(np.sum(A.indices[A.indptr[i]:A.indptr[i + 1]] != i)) for i in range(n)]
+    order = sorted(range(n), key=lambda i: (-deg[i], -int(h[i]), i))
     col = -np.ones(n, int)
     for i in order:
         nb = A.indices[A.indptr[i]:A.indptr[i + 1]]
