@@ -208,6 +208,7 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters, launches = [], 0
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed_solves")  # lets ncu --nvtx-include select them
         e0.record(stream)
         for _ in range(args.steps):
             st = step()
@@ -216,6 +217,7 @@ def main():
             assert st["status"][0] == 0, st
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if ws > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
@@ -246,25 +248,36 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_value = nh * sum(e_iters) * ws / e2e_s / 1e6
 
-    # roofline of the dominant kernel (the fine SpMV): algorithmic bytes per launch
-    # = 12 B per nonzero (FP64 value + int32 column) + 20 B per row (row pointer int64,
-    # x read once, y written) ; measured with CUDA events on the launching stream
+    # Rooflines, measured with CUDA events on the launching stream (pkasp_time_kernel).
+    # Dominant kernel by the launch list of a solve (profiles/launches_p3_n32_solve.md):
+    # the colour phases of the fine smoother S_k (about 63% of kernel time). Algorithmic
+    # bytes of one S_k application (all its phases): each off-diagonal entry once
+    # (FP64 value + int32 column = 12 B) and per row 52 B (inverse diagonal, r, y written
+    # then read-modified, two part pointers, row index); a phase's average rate is this
+    # total over the application's time. The fine SpMV: 12 B per nonzero + 20 B per row.
+    info64 = G.info
     spmv_ms = G.time_kernel(0, 50)
     smoother_ms = G.time_kernel(1, 20)
     nnz = int(G.info.nnz_h)
     spmv_bytes = 12 * nnz + 20 * nh
+    smoother_bytes = 12 * (nnz - nh) + 52 * nh
     pk = peaks()
     hbm = pk.get("hbm_gbs")
+    peak = hbm if hbm else 6800.0
+    src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback"
+    s_ach = smoother_bytes / (smoother_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_gs_phase (colour phases of the fine SGS S_k, FP64)",
+            "achieved": s_ach, "peak": peak, "unit": "GB/s", "frac": s_ach / peak, "traffic": None,
+            "peak_source": src, "bytes_per_application": smoother_bytes, "ms_per_application": smoother_ms,
+            "phases_per_application": 2 * int(info64.fine_colours) - 1,
+            "note": "FP64-pipe bound per phase (ncu: fp64 pipe 71% busy while active); "
+                    "see profiles/k_gs_phase_p3_n32.md"}
     achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_spmv (fine A_h SpMV, FP64 CSR)", "achieved": achieved,
-            "peak": hbm if hbm else 6800.0, "unit": "GB/s",
-            "frac": achieved / (hbm if hbm else 6800.0), "traffic": None,
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback",
-            "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms}
-    # one symmetric GS application from zero reads each off-diagonal entry once (value +
-    # column) and per row: diagonal, r, y (write, then read-modify-write), lptr/uptr, perm
-    smoother_bytes = 12 * (nnz - nh) + 52 * nh
-    info64 = G.info
+    roof_spmv = {"bound": "hbm", "kernel": "k_spmv_pq / k_sell_spmv (fine SpMV, SELL-32, FP64)",
+                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                 "traffic": 552.3e6 + 8.1e6, "traffic_source":
+                 "ncu dram__bytes_read+write of one k_spmv_pq launch, profiles/k_spmv_pq_sell_p3_n32.md",
+                 "peak_source": src, "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms}
     # the mixed-precision variant of the same solve: FP32 smoother / I_P / AMG, FP64 flexible CG
     G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, precond_precision=1, use_graph=0 if args.eager else 1)
     for _ in range(2):
@@ -302,7 +315,8 @@ def main():
                 "config": CONFIG, "clocks": clk.summary(),
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * nh,
                         "d2h_bytes_per_step": 8 * nh},
-                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu}
+                "gpu_launches": launches, "roofline": roof, "roofline_spmv": roof_spmv,
+                "cpu_baseline": cpu}
         line.update(extra)
         print(json.dumps(line))
     if ws > 1:
