@@ -1,5 +1,6 @@
 // api.cu -- the C ABI declared in include/pkasp.h. Converts internal exceptions into
 // status codes plus a per-thread message, validates arguments, and stages host arrays.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -254,17 +255,23 @@ static int solve_common(pkasp_problem *p, const double *b, double *x, int ncols,
     return guarded([&]() -> int {
         cudaStream_t s = (cudaStream_t)stream;
         const bool bd = is_device_ptr(b), xd = is_device_ptr(x);
-        pk::ensure_work(p, ncols);
+        pk::ensure_work(p, 1);
         const int64_t n = p->nh * ld;
+        if ((!bd || !xd) && p->stage_elems < n) {
+            p->stage_pool.free_all();
+            p->stage_b = p->stage_pool.get<double>(std::max<int64_t>(n, 1));
+            p->stage_x = p->stage_pool.get<double>(std::max<int64_t>(n, 1));
+            p->stage_elems = n;
+        }
         const double *bb = b;
         double *xx = x;
         if (!bd) {
-            PK_CUDA(cudaMemcpyAsync(p->w_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-            bb = p->w_b;
+            PK_CUDA(cudaMemcpyAsync(p->stage_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+            bb = p->stage_b;
         }
         if (!xd) {
-            PK_CUDA(cudaMemcpyAsync(p->w_x, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-            xx = p->w_x;
+            PK_CUDA(cudaMemcpyAsync(p->stage_x, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+            xx = p->stage_x;
         }
         int rc = pk::solve_device(p, bb, xx, ncols, ld, st, s);
         if (!xd) {
@@ -303,6 +310,7 @@ int pkasp_destroy(pkasp_problem *p) {
     if (!p) return PKASP_OK;
     cudaDeviceSynchronize();
     pk::free_setup(p);
+    p->stage_pool.free_all();
     p->pool.free_all();
     if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);

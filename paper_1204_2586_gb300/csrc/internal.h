@@ -195,6 +195,22 @@ struct pkasp_problem {
     const void *graph_key_b = nullptr;
     void *graph_key_x = nullptr;
     cudaStream_t graph_stream = nullptr;
+    // several right-hand sides: blocks [n][NC] (batched.cu), sized for one width NC
+    pk::DevPool bwork_pool;
+    int bwork_nc = -1, bwork_hist = 0;
+    double *bw_r = nullptr, *bw_z = nullptr, *bw_p = nullptr, *bw_q = nullptr, *bw_b = nullptr,
+           *bw_x = nullptr, *bw_zs = nullptr, *bw_t = nullptr, *bw_hist = nullptr;
+    float *bw_zs32 = nullptr, *bw_t32 = nullptr;
+    int *bw_mask = nullptr;
+    std::vector<double *> bl_b, bl_x, bl_r;  // per level
+    std::vector<float *> bl_b32, bl_x32, bl_r32;
+    cudaGraphExec_t bgraph_exec = nullptr;
+    cudaGraph_t bgraph = nullptr;
+    long long bg_init = 0, bg_body = 0, bg_final = 0;
+    // staging of host arrays [n][ld]
+    pk::DevPool stage_pool;
+    int64_t stage_elems = 0;
+    double *stage_b = nullptr, *stage_x = nullptr;
 };
 
 namespace pk {
@@ -240,6 +256,10 @@ void pmis_device(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_
 void pmis_noalloc(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_t *strong, uint64_t stream_id,
                   int8_t *cf, cudaStream_t s);
 void ensure_work(pkasp_problem *p, int ncols);
+// PCG on several right-hand sides (batched.cu); b and x device arrays [n_h][ld]
+int solve_batched(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld, pkasp_stats *st,
+                  cudaStream_t s);
+void free_batched(pkasp_problem *p);
 float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s);
 
 // SELL-32 builders (sell.cu)

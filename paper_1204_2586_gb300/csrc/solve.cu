@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(kBlock) k_true_residual(int64_t n, RowOp A, co
 // setup orchestration
 // ---------------------------------------------------------------------------------
 void free_setup(pkasp_problem *p) {
+    free_batched(p);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     p->graph_exec = nullptr;
@@ -859,8 +860,7 @@ void build_graph(pkasp_problem *p, const double *b, double *x) {
 
 int solve_device(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld, pkasp_stats *st,
                  cudaStream_t s) {
-    if (ncols != 1) fail(PKASP_EINVAL, "this build solves one right-hand side per call");
-    (void)ld;
+    if (ncols != 1 || ld != 1) return solve_batched(p, b, x, ncols, ld, st, s);
     ensure_work(p, 1);
     const int cap = (st && st->hist_cap > 0) ? st->hist_cap : 1;
     if (cap > p->hist_cap) {

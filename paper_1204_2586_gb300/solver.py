@@ -13,6 +13,20 @@ def _ptr(t) -> int:
     return t.data_ptr()
 
 
+def _row_stride(a) -> int:
+    """Elements between consecutive rows of a [n] or [n, ncols] array (the ABI's ld);
+    columns must be adjacent."""
+    if a.ndim == 1:
+        return 1
+    if hasattr(a, "stride") and callable(a.stride):
+        st = a.stride()
+    else:
+        st = tuple(s // a.itemsize for s in a.strides)
+    if a.shape[1] > 1 and st[1] != 1:
+        raise ValueError("columns of a multi-RHS block must be adjacent (stride 1)")
+    return st[0]
+
+
 def _stream(stream=None):
     import torch
 
@@ -121,6 +135,9 @@ class Problem:
         if x is None:
             x = torch.zeros_like(b) if isinstance(b, torch.Tensor) else np.zeros_like(b)
         ncols = 1 if b.ndim == 1 else b.shape[1]
+        ld = _row_stride(x)
+        if _row_stride(b) != ld:
+            raise ValueError("b and x must share one row stride (ld)")
         st = L.pkasp_stats()
         hist = None
         if hist_cap > 0:
@@ -129,7 +146,7 @@ class Problem:
             st.hist_cap = hist_cap
         bp = _ptr(b) if isinstance(b, torch.Tensor) else b.ctypes.data
         xp = _ptr(x) if isinstance(x, torch.Tensor) else x.ctypes.data
-        rc = L.load().pkasp_solve(self.h, bp, xp, ncols, ncols, C.byref(st), _stream(stream))
+        rc = L.load().pkasp_solve(self.h, bp, xp, ncols, ld, C.byref(st), _stream(stream))
         if rc not in (L.PKASP_OK, L.PKASP_ENOTCONV, L.PKASP_EBREAKDOWN) or (rc != L.PKASP_OK and raise_on_fail):
             L.check(rc)
         out = dict(rc=rc, iters=list(st.iters[:ncols]), status=list(st.status[:ncols]),
@@ -147,8 +164,11 @@ class Problem:
         if lam is None:
             lam = torch.zeros_like(g)
         ncols = 1 if g.ndim == 1 else g.shape[1]
+        ld = _row_stride(lam)
+        if _row_stride(g) != ld:
+            raise ValueError("g and lam must share one row stride (ld)")
         st = L.pkasp_stats()
-        L.check(L.load().pkasp_solve_adjoint(self.h, _ptr(g), _ptr(lam), ncols, ncols, C.byref(st),
+        L.check(L.load().pkasp_solve_adjoint(self.h, _ptr(g), _ptr(lam), ncols, ld, C.byref(st),
                                              _stream(stream)))
         return lam, dict(iters=list(st.iters[:ncols]), status=list(st.status[:ncols]),
                          true_rel=list(st.true_rel[:ncols]))
