@@ -8,6 +8,12 @@ The metric is MDOF*iter/s = n_h * iterations / solve time; the time to solution 
 HBM roofline of the dominant kernel are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload p3_n32 | p2_n64_batched48]
+
+The second workload is the multi-RHS solve: the P2 vector Laplacian (3 velocity
+components, identical scalar blocks) on a 64^3 jittered Kuhn mesh with 16 right-hand
+sides of i.i.d. N(0,1) entries (seed 2), i.e. 48 columns of the scalar system in one
+blocked PCG, FP32 preconditioner and FP64 outer iteration.
 
 Multi-GPU: the path runs as independent replicas (one solve per rank, no collective on
 the data path); value sums the ranks' work over the slowest rank's time.
@@ -39,6 +45,23 @@ CONFIG = {
     "l2_flush": "inputs larger than L2: A_h alone is 480 MB (12 B/nnz x 39,951,635 nnz) vs 129 MB L2",
     "parallelism": "replicas (one independent solve per GPU)",
 }
+BATCHED = dict(name="p2_n64_batched48", k=2, n=64, jitter=0.2, mesh_seed=0, rhs_seed=2, ncols=48)
+CONFIG_BATCHED = {
+    "workload": "P2 vector Laplacian (3 components x 16 right-hand sides = 48 columns of the scalar "
+                "system), kappa=1, 64^3 jittered Kuhn cubes (1,572,864 tets, 2,048,383 unknowns per column), "
+                "RHS entries i.i.d. N(0,1) (seed 2), one blocked PCG to rel. residual 1e-8 per column, "
+                "FP32 preconditioner (1 SGS sweep + 1 P1 AMG V-cycle, l1-Jacobi levels), FP64 outer "
+                "flexible CG, CUDA-graph loop",
+    "mesh": "unit cube, 64^3 cubes x 6 Kuhn tets, interior vertices jittered by <=0.2h (seed 0)",
+    "k": 2,
+    "n_h": 2048383,
+    "ncols": 48,
+    "l2_flush": "inputs larger than L2: every [n_h][48] FP64 block is 787 MB vs 129 MB L2",
+    "parallelism": "replicas (one independent blocked solve per GPU)",
+}
+# peak of the FP64 pipe derived from unit counts and clocks: 152 SMs x 2,070 MHz x 4 flop
+# per clock per SM (2 FP64 FMA per clock per SM) = 1.259 TFLOP/s (nominal 1.25)
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 ORACLE_SAMPLE_ITERS = 12
 # AMG level smoother: l1-Jacobi (1), one kernel per smoothing step; multicolour GS on the
 # dense coarse levels needs one launch per colour and costs ~25x more per V-cycle here
@@ -116,28 +139,36 @@ def make_problem():
     return xyz, t, Problem(xyz, t, WORKLOAD["k"])
 
 
-def run_cpu_oracle(steps, warmup, sample_iters=ORACLE_SAMPLE_ITERS):
+def run_cpu_oracle(steps, warmup, sample_iters=ORACLE_SAMPLE_ITERS, batched=False):
     """The oracle, as it stands, on the host: assembly and setup untimed, then timed
-    bounded samples of the solve (sample_iters PCG iterations each)."""
+    bounded samples of the solve (sample_iters PCG iterations each). The oracle solves
+    one right-hand side at a time; on the multi-RHS workload a sample is one column."""
     import oracle
-    from paper_1204_2586_gb300.inputs import kuhn_mesh
+    from paper_1204_2586_gb300.inputs import kuhn_mesh, rhs_normal
 
-    xyz, t = kuhn_mesh(WORKLOAD["n"], WORKLOAD["jitter"], WORKLOAD["mesh_seed"])
-    P = oracle.Problem(xyz, t, WORKLOAD["k"])
-    P.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, max_iter=sample_iters)
+    wl = BATCHED if batched else WORKLOAD
+    xyz, t = kuhn_mesh(wl["n"], wl["jitter"], wl["mesh_seed"])
+    P = oracle.Problem(xyz, t, wl["k"])
+    if batched:
+        P.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, max_iter=sample_iters, flexible=1)
+        b = rhs_normal(P.nh, 1, wl["rhs_seed"])[:, 0]
+    else:
+        P.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, max_iter=sample_iters)
+        b = None
     times, iters = [], []
     for i in range(warmup + steps):
         t0 = time.perf_counter()
-        out = P.solve()
+        out = P.solve(b)
         dt = time.perf_counter() - t0
         if i >= warmup:
             times.append(dt)
             iters.append(out["iters"])
     tot = sum(times)
     value = P.nh * sum(iters) / tot / 1e6
+    what = "one column (FP64 flexible CG)" if batched else "the solve"
     return value, dict(value=value, unit=UNIT, cores=1, kind="oracle",
-                       sample=f"{steps} timed solves of {sample_iters} PCG iterations each on the full "
-                              f"workload (n_h={P.nh}); single-threaded C oracle, assembly/setup untimed",
+                       sample=f"{steps} timed runs of {sample_iters} PCG iterations each of {what} on the "
+                              f"full workload (n_h={P.nh}); single-threaded C oracle, assembly/setup untimed",
                        seconds=tot)
 
 
@@ -145,11 +176,13 @@ def reference_arm(args):
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
         return
-    value, cpu = run_cpu_oracle(args.steps, args.warmup, sample_iters=4)
+    batched = args.workload == BATCHED["name"]
+    value, cpu = run_cpu_oracle(args.steps, args.warmup, sample_iters=4, batched=batched)
     ms = cpu["seconds"] / args.steps * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": CONFIG_BATCHED if batched else CONFIG,
             "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -162,6 +195,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD["name"], choices=[WORKLOAD["name"], BATCHED["name"]])
     ap.add_argument("--eager", action="store_true",
                     help="launch the same kernels without the CUDA graph (profilers cannot see "
                          "kernels inside graphs that hold conditional nodes)")
@@ -183,6 +217,11 @@ def main():
     from paper_1204_2586_gb300 import build
 
     build.build()
+    if args.workload == BATCHED["name"]:
+        run_batched(args, ws, rank, local)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
     t_as = time.perf_counter()
     xyz, tets, G = make_problem()
     torch.cuda.synchronize()
@@ -321,6 +360,156 @@ def main():
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_batched(args, ws, rank, local):
+    """One step = one blocked PCG solve of all 48 columns from X0 = 0. value counts every
+    column's iterations: n_h * sum_c iters_c / time."""
+    import numpy as np
+    import torch
+
+    from paper_1204_2586_gb300 import Problem
+    from paper_1204_2586_gb300.inputs import kuhn_mesh, rhs_normal
+
+    wl = BATCHED
+    t_as = time.perf_counter()
+    xyz, tets = kuhn_mesh(wl["n"], wl["jitter"], wl["mesh_seed"])
+    G = Problem(xyz, tets, wl["k"])
+    torch.cuda.synchronize()
+    assemble_s = time.perf_counter() - t_as
+    graph = 0 if args.eager else 1
+    t_su = time.perf_counter()
+    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, precond_precision=1, use_graph=graph)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_su
+    nh, nc = G.nh, wl["ncols"]
+    Bh = rhs_normal(nh, nc, wl["rhs_seed"])
+    B = torch.tensor(Bh, device="cuda")
+    X = torch.zeros_like(B)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        X.zero_()
+        _, st = G.solve(B, X)
+        return st
+
+    for _ in range(args.warmup):
+        st = step()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    col_iters, launches = [], 0
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed_solves")
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = step()
+            col_iters.append(sum(st["iters"]))
+            launches += st["kernel_launches"]
+            assert st["rc"] == 0 and all(v == 0 for v in st["status"]), st
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nh * sum(col_iters) * ws / (ms / 1e3) / 1e6
+    sol_s = ms / 1e3 / args.steps
+    info = G.info
+    max_true_rel = max(st["true_rel"])
+
+    # end to end through the C ABI with pinned host blocks: H2D of B and X0, D2H of X
+    bh = torch.empty((nh, nc), dtype=torch.float64, pin_memory=True)
+    bh.copy_(torch.from_numpy(Bh))
+    xh = torch.zeros((nh, nc), dtype=torch.float64, pin_memory=True)
+    bnp, xnp = bh.numpy(), xh.numpy()
+    for _ in range(2):
+        xnp[:] = 0.0
+        G.solve(bnp, xnp)
+    torch.cuda.synchronize()
+    e_iters = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xnp[:] = 0.0
+        _, st = G.solve(bnp, xnp)
+        e_iters.append(sum(st["iters"]))
+    e2e_s = time.perf_counter() - t0
+    e2e_value = nh * sum(e_iters) * ws / e2e_s / 1e6
+
+    # roofline of the dominant kernel, the blocked FP64 SpMM Q = A_h P with its per-column
+    # dot (P, Q): 48 FP64 FMA per stored entry and column, so it is bound by the FP64 pipe
+    # (algorithmic flops 2 nnz NC + 2 n NC), not by HBM (12 nnz + 24 n NC bytes)
+    nnz = int(info.nnz_h)
+    spmm_ms = G.time_kernel(4, 10)
+    flops = 2.0 * nnz * nc + 2.0 * nh * nc
+    ach = flops / (spmm_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "kb_spmv_pq<48> (blocked FP64 SpMM + per-column dot)",
+            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+            "traffic": None, "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM",
+            "flops_per_launch": flops, "ms_per_launch": spmm_ms,
+            "hbm_bytes_per_launch": 12 * nnz + 20 * nh + 16 * nh * nc}
+    # the blocked FP32 fine smoother (all colour phases of one S_k application on 48
+    # columns): algorithmic bytes 8 per off-diagonal entry (FP32 value + int32 column),
+    # per row 20 B of indices/inverse diagonal and per row and column 8 B of r (FP64),
+    # 4 B of y written forward, 8 B of y read and rewritten backward
+    sm_ms = G.time_kernel(5, 5)
+    layout = (int(G.info.block_width), int(G.info.block_group), int(G.info.block_lanes))
+    sm_bytes = 8 * (nnz - nh) + 20 * nh + 20 * nh * nc
+    pk = peaks()
+    hbm = pk.get("hbm_gbs") or 6800.0
+    roof_sm = {"bound": "hbm", "kernel": "kb_gs_phase<*, float> (blocked FP32 fine SGS)",
+               "achieved": sm_bytes / (sm_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+               "frac": sm_bytes / (sm_ms / 1e3) / 1e9 / hbm, "traffic": None,
+               "ms_per_application": sm_ms, "bytes_per_application": sm_bytes,
+               "column_group": layout[1], "lanes_per_row": layout[2]}
+    prec_ms = G.time_kernel(6, 5)
+
+    # the same block with an FP64 preconditioner, and one column solved alone
+    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, precond_precision=0, use_graph=graph)
+    for _ in range(2):
+        st64 = step()
+    ms64 = min(step()["solve_ms"] for _ in range(3))
+    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, precond_precision=1, use_graph=graph)
+    b1 = B[:, 0].contiguous()
+    x1 = torch.zeros_like(b1)
+    for _ in range(2):
+        x1.zero_()
+        G.solve(b1, x1)
+    one = []
+    for _ in range(3):
+        x1.zero_()
+        one.append(G.solve(b1, x1)[1]["solve_ms"])
+    extra = {"time_to_solution_s": sol_s, "column_iterations_min": min(st["iters"]),
+             "column_iterations_max": max(st["iters"]), "max_true_rel_residual": max_true_rel,
+             "setup_s": setup_s, "assemble_s": assemble_s, "levels": int(info.levels),
+             "fine_colours": int(info.fine_colours), "block_width": layout[0],
+             "preconditioner_ms": prec_ms,
+             "fp64_precond_time_to_solution_s": ms64 / 1e3,
+             "single_column_time_to_solution_s": min(one) / 1e3,
+             "speedup_vs_48_single_column_solves": 48 * min(one) / 1e3 / sol_s}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            _, cpu = run_cpu_oracle(1, 0, sample_iters=6, batched=True)
+            cpu.pop("seconds", None)
+        except Exception as e:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": CONFIG_BATCHED, "clocks": clk.summary(),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * nh * nc,
+                        "d2h_bytes_per_step": 8 * nh * nc},
+                "gpu_launches": launches, "roofline": roof, "roofline_smoother": roof_sm,
+                "cpu_baseline": cpu}
+        line.update(extra)
+        print(json.dumps(line))
 
 
 if __name__ == "__main__":

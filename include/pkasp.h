@@ -98,6 +98,11 @@ typedef struct {
     int spmv_layout;        /* autotuned layout of the fine SpMV: 0 = SELL-32 (one thread
                                per row), t > 0 = CSR read by t lanes per row */
     int smoother_layout;    /* same for the fine smoother's colour phases */
+    int block_width;        /* columns of the internal multi-RHS blocks (4, 8, 16, 32, 48
+                               or 64) of the last solve with ncols > 1; 0 before one */
+    int block_group;        /* columns per group of the multi-RHS fine smoother phases,
+                               autotuned at the first solve of a width (0 before) */
+    int block_lanes;        /* threads per row of those phases (autotuned with it) */
 } pkasp_info;
 
 /* Per-solve statistics, filled by pkasp_solve (which synchronises the stream). */
@@ -277,7 +282,10 @@ int pkasp_reference_tensors(int k, double *S_out);
 
 /* Average device time (ms, CUDA events on `stream`) of `reps` back-to-back launches of
  * one hot-path kernel of the current setup: which = 0 fine SpMV, 1 fine smoother
- * (all colour phases of one S_k application), 2 V-cycle, 3 whole preconditioner. */
+ * (all colour phases of one S_k application), 2 V-cycle, 3 whole preconditioner; on the
+ * multi-RHS blocks of the last solve with ncols > 1 (ESTATE before one): 4 blocked SpMM
+ * Q = A_h P with its per-column dot (P, Q), 5 blocked fine smoother, 6 blocked
+ * preconditioner. The blocked timings overwrite the solve's work blocks and scalars. */
 int pkasp_time_kernel(pkasp_problem *p, int which, int reps, float *ms_out,
                       pkasp_stream_t stream);
 

@@ -39,7 +39,8 @@ class pkasp_info(C.Structure):
                 ("level_rows", C.c_int64 * MAX_LEVELS), ("level_nnz", C.c_int64 * MAX_LEVELS),
                 ("level_colours", C.c_int * MAX_LEVELS), ("op_complexity", C.c_double),
                 ("setup_ms", C.c_double), ("assemble_ms", C.c_double),
-                ("spmv_layout", C.c_int), ("smoother_layout", C.c_int)]
+                ("spmv_layout", C.c_int), ("smoother_layout", C.c_int),
+                ("block_width", C.c_int), ("block_group", C.c_int), ("block_lanes", C.c_int)]
 
 
 class pkasp_stats(C.Structure):

@@ -189,6 +189,9 @@ int pkasp_problem_info(const pkasp_problem *p, pkasp_info *info) {
         info->setup_ms = p->setup_ms;
         info->spmv_layout = p->spmv_tpr;
         info->smoother_layout = p->fine_tpr;
+        info->block_width = p->bwork_nc > 0 ? p->bwork_nc : 0;
+        info->block_group = p->bgroup_cols;
+        info->block_lanes = p->blanes;
     }
     return PKASP_OK;
 }

@@ -198,9 +198,11 @@ struct pkasp_problem {
     // several right-hand sides: blocks [n][NC] (batched.cu), sized for one width NC
     pk::DevPool bwork_pool;
     int bwork_nc = -1, bwork_hist = 0;
+    int bchunk = 0;  // 1 + the autotuned layout of the blocked fine smoother (0: not tuned yet)
+    int bgroup_cols = 0, blanes = 0;  // that layout: columns per group, lanes per row
     double *bw_r = nullptr, *bw_z = nullptr, *bw_p = nullptr, *bw_q = nullptr, *bw_b = nullptr,
            *bw_x = nullptr, *bw_zs = nullptr, *bw_t = nullptr, *bw_hist = nullptr;
-    float *bw_zs32 = nullptr, *bw_t32 = nullptr;
+    float *bw_zs32 = nullptr, *bw_t32 = nullptr, *bw_r32 = nullptr;
     int *bw_mask = nullptr;
     std::vector<double *> bl_b, bl_x, bl_r;  // per level
     std::vector<float *> bl_b32, bl_x32, bl_r32;
@@ -260,6 +262,7 @@ void ensure_work(pkasp_problem *p, int ncols);
 int solve_batched(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld, pkasp_stats *st,
                   cudaStream_t s);
 void free_batched(pkasp_problem *p);
+float time_batched(pkasp_problem *p, int which, int reps, cudaStream_t s);
 float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s);
 
 // SELL-32 builders (sell.cu)

@@ -940,6 +940,7 @@ int solve_device(pkasp_problem *p, const double *b, double *x, int ncols, int64_
 
 float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s) {
     if (reps < 1) reps = 1;
+    if (which >= 4) return time_batched(p, which, reps, s);
     cudaEvent_t e0, e1;
     PK_CUDA(cudaEventCreate(&e0));
     PK_CUDA(cudaEventCreate(&e1));

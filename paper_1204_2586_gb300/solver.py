@@ -52,10 +52,15 @@ class Problem:
         self.h = h
         self.k = k
         self.nt = nt
-        self.info = self._info()
-        self.nh = int(self.info.n_h)
-        self.nH = int(self.info.n_H)
+        inf = self._info()
+        self.nh = int(inf.n_h)
+        self.nH = int(inf.n_H)
         self.opts = None
+
+    @property
+    def info(self):
+        """pkasp_info of the problem as it is now (sizes, hierarchy, autotuned layouts)."""
+        return self._info()
 
     def _info(self):
         inf = L.pkasp_info()
@@ -124,7 +129,6 @@ class Problem:
         o = L.default_options(**kw)
         L.check(L.load().pkasp_setup(self.h, C.byref(o), _stream(stream)))
         self.opts = o
-        self.info = self._info()
         return self
 
     def solve(self, b, x=None, hist_cap=0, stream=None, raise_on_fail=True):
