@@ -139,14 +139,16 @@ def make_problem():
     return xyz, t, Problem(xyz, t, WORKLOAD["k"])
 
 
-def run_cpu_oracle(steps, warmup, sample_iters=ORACLE_SAMPLE_ITERS, batched=False):
+def run_cpu_oracle(steps, warmup, sample_iters=ORACLE_SAMPLE_ITERS, batched=False, mesh_n=0):
     """The oracle, as it stands, on the host: assembly and setup untimed, then timed
     bounded samples of the solve (sample_iters PCG iterations each). The oracle solves
     one right-hand side at a time; on the multi-RHS workload a sample is one column."""
     import oracle
     from paper_1204_2586_gb300.inputs import kuhn_mesh, rhs_normal
 
-    wl = BATCHED if batched else WORKLOAD
+    wl = dict(BATCHED if batched else WORKLOAD)
+    if mesh_n:
+        wl["n"] = mesh_n
     xyz, t = kuhn_mesh(wl["n"], wl["jitter"], wl["mesh_seed"])
     P = oracle.Problem(xyz, t, wl["k"])
     if batched:
@@ -196,10 +198,15 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD["name"], choices=[WORKLOAD["name"], BATCHED["name"]])
+    ap.add_argument("--mesh-n", type=int, default=0,
+                    help="cubes per side of the mesh instead of the workload's own (a smaller case "
+                         "of the same kernels for profiler captures; the JSON line states the size)")
     ap.add_argument("--eager", action="store_true",
                     help="launch the same kernels without the CUDA graph (profilers cannot see "
                          "kernels inside graphs that hold conditional nodes)")
     args = ap.parse_args()
+    if args.mesh_n and args.workload != BATCHED["name"]:
+        ap.error("--mesh-n applies to the multi-RHS workload only")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -371,7 +378,11 @@ def run_batched(args, ws, rank, local):
     from paper_1204_2586_gb300 import Problem
     from paper_1204_2586_gb300.inputs import kuhn_mesh, rhs_normal
 
-    wl = BATCHED
+    wl = dict(BATCHED)
+    config = dict(CONFIG_BATCHED)
+    if args.mesh_n:
+        wl["n"] = args.mesh_n
+        config["workload"] = f"{wl['n']}^3-cube case of: " + config["workload"]
     t_as = time.perf_counter()
     xyz, tets = kuhn_mesh(wl["n"], wl["jitter"], wl["mesh_seed"])
     G = Problem(xyz, tets, wl["k"])
@@ -383,6 +394,7 @@ def run_batched(args, ws, rank, local):
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_su
     nh, nc = G.nh, wl["ncols"]
+    config["n_h"] = nh
     Bh = rhs_normal(nh, nc, wl["rhs_seed"])
     B = torch.tensor(Bh, device="cuda")
     X = torch.zeros_like(B)
@@ -495,7 +507,7 @@ def run_batched(args, ws, rank, local):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            _, cpu = run_cpu_oracle(1, 0, sample_iters=6, batched=True)
+            _, cpu = run_cpu_oracle(1, 0, sample_iters=6, batched=True, mesh_n=args.mesh_n)
             cpu.pop("seconds", None)
         except Exception as e:
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
@@ -503,7 +515,7 @@ def run_batched(args, ws, rank, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": CONFIG_BATCHED, "clocks": clk.summary(),
+                "config": config, "clocks": clk.summary(),
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * nh * nc,
                         "d2h_bytes_per_step": 8 * nh * nc},
                 "gpu_launches": launches, "roofline": roof, "roofline_smoother": roof_sm,
