@@ -341,7 +341,9 @@ def main():
              "fine_colours": int(info64.fine_colours), "op_complexity": info64.op_complexity,
              "spmv_layout": "SELL-32" if info64.spmv_layout == 0 else f"CSR x{info64.spmv_layout} lanes",
              "smoother_layout": ("SELL-32" if info64.smoother_layout == 0 else
-                                 "CSR, lanes per colour" if info64.smoother_layout < 0 else
+                                 "CSR, lanes per colour" if info64.smoother_layout == -1 else
+                                 f"one cooperative launch, CSR x{-info64.smoother_layout} lanes"
+                                 if info64.smoother_layout < -1 else
                                  f"CSR x{info64.smoother_layout} lanes"),
              "smoother_ms": smoother_ms,
              "smoother_GBps": smoother_bytes / (smoother_ms / 1e3) / 1e9}

@@ -77,7 +77,13 @@ typedef struct {
                              while loop; 0: eager launches, host checks every iteration [1] */
     int spmv_threads;     /* threads per row of the fine SpMV and smoother: 4, 8, 16 or
                              32; 0 = pick by mean row length [0] */
-    int reserved[7];
+    int smoother_layout;  /* fine smoother layout (SGS): 0 = autotuned at setup [0];
+                             1 = one launch per colour phase, CSR, lanes fitted per colour;
+                             2 = per phase, SELL-32; 4, 8, 16 = per phase, CSR with that
+                             many lanes per row; -4, -8, -16 = the whole symmetric sweep
+                             in one cooperative launch with that many lanes per row.
+                             spmv_threads != 0 overrides it with its own lane count. */
+    int reserved[6];
 } pkasp_options;
 
 /* Problem sizes after assembly and (for the AMG entries) after setup. */
@@ -97,7 +103,9 @@ typedef struct {
     double setup_ms, assemble_ms;
     int spmv_layout;        /* autotuned layout of the fine SpMV: 0 = SELL-32 (one thread
                                per row), t > 0 = CSR read by t lanes per row */
-    int smoother_layout;    /* same for the fine smoother's colour phases */
+    int smoother_layout;    /* same for the fine smoother's colour phases; -1 = CSR with
+                               lanes fitted per colour; -t (t > 1) = the whole symmetric
+                               sweep in one cooperative launch, t lanes per row */
     int block_width;        /* columns of the internal multi-RHS blocks (4, 8, 16, 32, 48
                                or 64) of the last solve with ncols > 1; 0 before one */
     int block_group;        /* columns per group of the multi-RHS fine smoother phases,

@@ -28,7 +28,7 @@ class pkasp_options(C.Structure):
                 ("level_smoother", C.c_int), ("coarse_size", C.c_int), ("max_levels", C.c_int),
                 ("seed", C.c_uint64), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("flexible", C.c_int), ("precond_precision", C.c_int), ("use_graph", C.c_int),
-                ("spmv_threads", C.c_int), ("reserved", C.c_int * 7)]
+                ("spmv_threads", C.c_int), ("smoother_layout", C.c_int), ("reserved", C.c_int * 6)]
 
 
 class pkasp_info(C.Structure):

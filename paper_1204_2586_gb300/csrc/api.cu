@@ -72,6 +72,7 @@ void pkasp_default_options(pkasp_options *o) {
     o->precond_precision = PKASP_PREC_FP64;
     o->use_graph = 1;
     o->spmv_threads = 0;
+    o->smoother_layout = 0;
 }
 
 int pkasp_last_error(char *buf, size_t n) {
@@ -240,6 +241,11 @@ int pkasp_setup(pkasp_problem *p, const pkasp_options *opt, pkasp_stream_t strea
     if (o.spmv_threads != 0 && o.spmv_threads != 4 && o.spmv_threads != 8 && o.spmv_threads != 16 &&
         o.spmv_threads != 32)
         return set_error(PKASP_EINVAL, "spmv_threads must be 0, 4, 8, 16 or 32");
+    {
+        const int l = o.smoother_layout;
+        if (!(l == 0 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == -4 || l == -8 || l == -16))
+            return set_error(PKASP_EINVAL, "smoother_layout must be 0, 1, 2, 4, 8, 16, -4, -8 or -16");
+    }
     return guarded([&]() -> int {
         auto t0 = std::chrono::steady_clock::now();
         p->opt = o;
@@ -336,6 +342,7 @@ int pkasp_apply_prec(pkasp_problem *p, const double *r_dev, double *z_dev, pkasp
     if (!p->have_setup) return set_error(PKASP_ESTATE, "setup first");
     return guarded([&]() -> int {
         pk::apply_prec(p, r_dev, z_dev, (cudaStream_t)stream);
+        if (p->fine_tpr < -1) pk::check_barrier(p, (cudaStream_t)stream);
         return PKASP_OK;
     });
 }
@@ -345,6 +352,7 @@ int pkasp_apply_smoother(pkasp_problem *p, const double *r_dev, double *z_dev, p
     if (!p->have_setup) return set_error(PKASP_ESTATE, "setup first");
     return guarded([&]() -> int {
         pk::apply_smoother(p, r_dev, z_dev, (cudaStream_t)stream);
+        if (p->fine_tpr < -1) pk::check_barrier(p, (cudaStream_t)stream);
         return PKASP_OK;
     });
 }

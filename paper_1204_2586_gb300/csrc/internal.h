@@ -73,6 +73,7 @@ struct DSplit {
     float *lval32 = nullptr, *uval32 = nullptr, *diag32 = nullptr;
     int64_t nnz_l = 0, nnz_u = 0;
     std::vector<int> lmax, umax;  // per colour: longest lower / upper part (host)
+    std::vector<int> l90, u90;    // per colour: 90th percentile of those lengths (host)
 };
 
 // SELL-32: slices of 32 rows (one thread per row), entries column-major within a slice
@@ -169,6 +170,9 @@ struct pkasp_problem {
     double *d_cinv = nullptr;  // dense inverse of the coarsest matrix
     float *d_cinv32 = nullptr;
     int64_t nc = 0;
+    int64_t *d_fine_off = nullptr;  // device copy of fine.off (persistent smoother)
+    unsigned *d_bar = nullptr;      // grid-barrier arrivals / exits of the persistent smoother
+    int *d_bar_err = nullptr;       // set when one of its barriers timed out
     int spmv_tpr = 4;   // lanes per row of the fine SpMV (autotuned at setup)
     int fine_tpr = 4;   // lanes per row of the fine smoother phases (autotuned at setup)
     // solve work (sized for ncols = 1 at setup, grown on demand)
@@ -258,6 +262,7 @@ void pmis_device(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_
 void pmis_noalloc(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_t *strong, uint64_t stream_id,
                   int8_t *cf, cudaStream_t s);
 void ensure_work(pkasp_problem *p, int ncols);
+void check_barrier(pkasp_problem *p, cudaStream_t s);
 // PCG on several right-hand sides (batched.cu); b and x device arrays [n_h][ld]
 int solve_batched(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld, pkasp_stats *st,
                   cudaStream_t s);

@@ -183,9 +183,12 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 //   BACK = false: y_i = (r_i - sum_L a_ij y_j) / a_ii
 //   BACK = true:  y_i = y_i - (sum_U a_ij y_j) / a_ii
 // Static loads (position, bounds, diagonal, first batch of the row's entries) happen
-// before the dependency wait, so they overlap the previous phase. Lane `sub` adds its
-// entries in the same order as row_dot.
-template <int TPR, typename PT, typename TR, bool BACK>
+// before the dependency wait, so they overlap the previous phase. A lane takes NB
+// entries per batch (entries sub, sub + TPR, ...): NB is fitted to the colour's longest
+// row part, because every FMA slot of a batch is issued whether its entry exists or not
+// and GB300's FP64 pipe is narrow. Lane `sub` adds its entries in ascending order for
+// every NB, so the result does not depend on NB.
+template <int TPR, int NB, typename PT, typename TR, bool BACK>
 __global__ void __launch_bounds__(kBlock) k_gs_phase(int64_t pb, int64_t pe, const int32_t *__restrict__ perm,
                                                      const int64_t *__restrict__ xptr, const int32_t *__restrict__ xcol,
                                                      const PT *__restrict__ xval, const PT *__restrict__ dinv,
@@ -199,11 +202,11 @@ __global__ void __launch_bounds__(kBlock) k_gs_phase(int64_t pb, int64_t pe, con
     const int32_t i = lead ? perm[p] : 0;
     const PT di = lead ? dinv[p] : PT(1);
     const int64_t lo = ok ? xptr[p] : 0, hi = ok ? xptr[p + 1] : 0;
-    int c[kBatch];
-    PT v[kBatch];
+    int c[NB];
+    PT v[NB];
     const int64_t b0 = lo + sub;
 #pragma unroll
-    for (int k = 0; k < kBatch; ++k) {
+    for (int k = 0; k < NB; ++k) {
         const int64_t e = b0 + (int64_t)k * TPR;
         const bool in = e < hi;
         c[k] = in ? __ldg(&xcol[e]) : -1;
@@ -214,18 +217,18 @@ __global__ void __launch_bounds__(kBlock) k_gs_phase(int64_t pb, int64_t pe, con
     if (lead) own = BACK ? y[i] : (PT)r[i];
     PT acc = PT(0);
 #pragma unroll
-    for (int k = 0; k < kBatch; ++k)
+    for (int k = 0; k < NB; ++k)
         if (c[k] >= 0) acc += v[k] * y[c[k]];
-    for (int64_t base = b0 + (int64_t)kBatch * TPR; base < hi; base += (int64_t)kBatch * TPR) {
+    for (int64_t base = b0 + (int64_t)NB * TPR; base < hi; base += (int64_t)NB * TPR) {
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
+        for (int k = 0; k < NB; ++k) {
             const int64_t e = base + (int64_t)k * TPR;
             const bool in = e < hi;
             c[k] = in ? __ldg(&xcol[e]) : -1;
             v[k] = in ? __ldg(&xval[e]) : PT(0);
         }
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k)
+        for (int k = 0; k < NB; ++k)
             if (c[k] >= 0) acc += v[k] * y[c[k]];
     }
     acc = subwarp_sum<TPR>(acc);

@@ -661,11 +661,27 @@ void build_split(DevPool &pool, const DCSR &A, uint64_t stream, bool want32, DSp
             PK_CUDA(cudaStreamSynchronize(s));
             sp.lmax.assign(sp.ncol, 0);
             sp.umax.assign(sp.ncol, 0);
-            for (int c = 0; c < sp.ncol; ++c)
+            sp.l90.assign(sp.ncol, 0);
+            sp.u90.assign(sp.ncol, 0);
+            std::vector<int> ll, ul;
+            for (int c = 0; c < sp.ncol; ++c) {
+                ll.clear();
+                ul.clear();
                 for (int64_t q = sp.off[c]; q < sp.off[c + 1]; ++q) {
-                    sp.lmax[c] = std::max<int>(sp.lmax[c], (int)(hl[q + 1] - hl[q]));
-                    sp.umax[c] = std::max<int>(sp.umax[c], (int)(hu[q + 1] - hu[q]));
+                    ll.push_back((int)(hl[q + 1] - hl[q]));
+                    ul.push_back((int)(hu[q + 1] - hu[q]));
+                    sp.lmax[c] = std::max<int>(sp.lmax[c], ll.back());
+                    sp.umax[c] = std::max<int>(sp.umax[c], ul.back());
                 }
+                // 90th percentile: the length one batch of loads should cover
+                if (!ll.empty()) {
+                    const size_t k = (ll.size() * 9) / 10;
+                    std::nth_element(ll.begin(), ll.begin() + k, ll.end());
+                    std::nth_element(ul.begin(), ul.begin() + k, ul.end());
+                    sp.l90[c] = ll[k];
+                    sp.u90[c] = ul[k];
+                }
+            }
         }
         sp.lcol = pool.get<int32_t>(sp.nnz_l > 0 ? sp.nnz_l : 1);
         sp.lval = pool.get<double>(sp.nnz_l > 0 ? sp.nnz_l : 1);

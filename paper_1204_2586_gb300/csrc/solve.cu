@@ -13,6 +13,7 @@
 
 #include "internal.h"
 #include "kernels.cuh"
+#include "persist.cuh"
 
 namespace pk {
 
@@ -113,6 +114,22 @@ int lanes_for(int len) {
     return t;
 }
 
+// Entries per lane and batch for a colour phase with tpr lanes whose row parts mostly
+// (90th percentile) have at most `len` entries: the fewest of 2, 4, 8 that cover such a
+// row in one batch (else 8); longer rows take further batches.
+int batch_for(int tpr, int len) {
+    for (int nb : {2, 4})
+        if (nb * tpr >= len) return nb;
+    return 8;
+}
+
+#define PK_NB_SWITCH(nb, BODY)                           \
+    switch (nb) {                                        \
+        case 2: { constexpr int NB = 2; BODY; } break;   \
+        case 4: { constexpr int NB = 4; BODY; } break;   \
+        default: { constexpr int NB = 8; BODY; } break;  \
+    }
+
 // colour phases of a forward sweep from zero: y = (D+L)^{-1} r; tpr < 0 picks the lanes
 // per colour from the colour's longest lower part
 template <typename PT, typename TR>
@@ -121,10 +138,12 @@ void gs_forward0(const DSplit &sp, int tpr_fixed, const TR *r, PT *y, cudaStream
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
         const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(sp.lmax[c]);
-        PK_TPR_SWITCH(tpr, (launch_pdl(k_gs_phase<TPR, PT, TR, false>, rows_grid(pe - pb, TPR), s, pb, pe,
-                                       (const int32_t *)sp.perm, (const int64_t *)sp.lptr,
-                                       (const int32_t *)sp.lcol, pick<PT>(sp.lval, sp.lval32),
-                                       pick<PT>(sp.dinv, sp.dinv32), r, y)));
+        const int nb = batch_for(tpr, sp.l90[c]);
+        PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl(k_gs_phase<TPR, NB, PT, TR, false>,
+                                                        rows_grid(pe - pb, TPR), s, pb, pe,
+                                                        (const int32_t *)sp.perm, (const int64_t *)sp.lptr,
+                                                        (const int32_t *)sp.lcol, pick<PT>(sp.lval, sp.lval32),
+                                                        pick<PT>(sp.dinv, sp.dinv32), r, y))));
     }
 }
 
@@ -136,10 +155,12 @@ void gs_backward0(const DSplit &sp, int tpr_fixed, PT *y, cudaStream_t s) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
         const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(sp.umax[c]);
-        PK_TPR_SWITCH(tpr, (launch_pdl(k_gs_phase<TPR, PT, PT, true>, rows_grid(pe - pb, TPR), s, pb, pe,
-                                       (const int32_t *)sp.perm, (const int64_t *)sp.uptr,
-                                       (const int32_t *)sp.ucol, pick<PT>(sp.uval, sp.uval32),
-                                       pick<PT>(sp.dinv, sp.dinv32), (const PT *)y, y)));
+        const int nb = batch_for(tpr, sp.u90[c]);
+        PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl(k_gs_phase<TPR, NB, PT, PT, true>,
+                                                        rows_grid(pe - pb, TPR), s, pb, pe,
+                                                        (const int32_t *)sp.perm, (const int64_t *)sp.uptr,
+                                                        (const int32_t *)sp.ucol, pick<PT>(sp.uval, sp.uval32),
+                                                        pick<PT>(sp.dinv, sp.dinv32), (const PT *)y, y))));
     }
 }
 
@@ -219,6 +240,48 @@ void vcycle(pkasp_problem *p, int l, cudaStream_t s) {
     }
 }
 
+// the symmetric sweep of the fine split as one cooperative launch (persist.cuh), TPR
+// lanes per row, kPersistBlocksPerSm blocks of kPersistBlock threads per SM
+constexpr int kPersistBlocksPerSm = 1;
+
+template <int TPR, typename PT, typename TR>
+void sgs_persistent(pkasp_problem *p, const TR *r, PT *y, cudaStream_t s) {
+    auto kern = k_sgs_persistent<TPR, PT, TR>;
+    int occ = 0, sms = 0, dev = 0;
+    PK_CUDA(cudaGetDevice(&dev));
+    PK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPersistBlock, 0));
+    if (occ < 1) fail(PKASP_ECUDA, "persistent smoother does not fit on an SM");
+    const DSplit &sp = p->fine;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(sms * std::min(occ, kPersistBlocksPerSm)));
+    cfg.blockDim = dim3(kPersistBlock);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PK_CUDA(cudaLaunchKernelEx(&cfg, kern, sp.ncol, (const int64_t *)p->d_fine_off, (const int32_t *)sp.perm,
+                               (const int64_t *)sp.lptr, (const int32_t *)sp.lcol, pick<PT>(sp.lval, sp.lval32),
+                               (const int64_t *)sp.uptr, (const int32_t *)sp.ucol, pick<PT>(sp.uval, sp.uval32),
+                               pick<PT>(sp.dinv, sp.dinv32), r, y, p->d_bar, p->d_bar_err));
+    PK_LAUNCH();
+}
+
+// reads (and clears) the persistent smoother's barrier-timeout flag; synchronises s
+void barrier_status(pkasp_problem *p, cudaStream_t s) {
+    if (!p->d_bar_err) return;
+    int err = 0;
+    PK_CUDA(cudaMemcpyAsync(&err, p->d_bar_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaStreamSynchronize(s));
+    if (err) {
+        PK_CUDA(cudaMemsetAsync(p->d_bar_err, 0, sizeof(int), s));
+        PK_CUDA(cudaStreamSynchronize(s));
+        fail(PKASP_ECUDA, "the persistent smoother's grid barrier timed out");
+    }
+}
+
 // S_k r from zero into zs (PT)
 template <typename PT>
 void smoother(pkasp_problem *p, const double *r, PT *zs, cudaStream_t s) {
@@ -228,6 +291,15 @@ void smoother(pkasp_problem *p, const double *r, PT *zs, cudaStream_t s) {
         return;
     }
     const int ts = p->fine_tpr;
+    if (ts < -1) {
+        // one cooperative launch for all colour phases, -ts lanes per row
+        switch (-ts) {
+            case 4: sgs_persistent<4, PT, double>(p, r, zs, s); break;
+            case 16: sgs_persistent<16, PT, double>(p, r, zs, s); break;
+            default: sgs_persistent<8, PT, double>(p, r, zs, s); break;
+        }
+        return;
+    }
     if (ts == 0) {
         // SELL-32 colour phases: colour c is the slice range [coff[c], coff[c+1])
         const DSell &L = p->fsl, &U = p->fsu;
@@ -559,6 +631,9 @@ void free_setup(pkasp_problem *p) {
     p->d_l1h = nullptr;
     p->d_l1h32 = nullptr;
     p->d_cinv = nullptr;
+    p->d_fine_off = nullptr;
+    p->d_bar = nullptr;
+    p->d_bar_err = nullptr;
     p->d_cinv32 = nullptr;
     p->work_cols = 0;
     p->have_setup = false;
@@ -572,6 +647,9 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
         p->spmv_tpr = p->fine_tpr = p->opt.spmv_threads;
         return;
     }
+    // a fixed smoother layout: internal code -1 per-colour lanes, 0 SELL-32, t lanes
+    const int fixed_fine = p->opt.smoother_layout == 1 ? -1 : p->opt.smoother_layout == 2 ? 0
+                                                                                           : p->opt.smoother_layout;
     cudaEvent_t e0, e1;
     PK_CUDA(cudaEventCreate(&e0));
     PK_CUDA(cudaEventCreate(&e1));
@@ -588,7 +666,8 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
     // 0: SELL-32, one thread per row; t > 0: CSR with t lanes per row; -1 (smoother
     // only): CSR with the lanes of each colour phase fitted to its longest row
     const int cand_spmv[] = {0, 2, 4, 8};
-    const int cand_fine[] = {-1, 0, 4, 8, 16};
+    // -t < -1: the whole sweep in one cooperative launch with t lanes per row
+    const int cand_fine[] = {-1, 0, 4, 8, 16, -4, -8, -16};
     float best = 1e30f;
     int pick_spmv = 0, pick_fine = -1;
     for (int t : cand_spmv) {
@@ -597,12 +676,21 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
         if (ms < best) best = ms, pick_spmv = t;
     }
     best = 1e30f;
-    if (p->opt.smoother == PKASP_SMOOTHER_SGS) {
+    if (p->opt.smoother == PKASP_SMOOTHER_SGS && p->opt.smoother_layout != 0) {
+        pick_fine = fixed_fine;
+    } else if (p->opt.smoother == PKASP_SMOOTHER_SGS) {
         for (int t : cand_fine) {
             p->fine_tpr = t;
             float ms = (p->opt.precond_precision == PKASP_PREC_FP32)
                            ? timed([&] { smoother<float>(p, p->d_b, p->w_zs32, s); })
                            : timed([&] { smoother<double>(p, p->d_b, p->w_zs, s); });
+            if (t < -1) {
+                try {
+                    barrier_status(p, s);
+                } catch (const Error &) {
+                    continue;  // a candidate whose barrier gave up is not taken
+                }
+            }
             if (ms < best) best = ms, pick_fine = t;
         }
     }
@@ -683,6 +771,14 @@ void setup_device(pkasp_problem *p, cudaStream_t s) {
     if (!p->ev_fork) PK_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     if (!p->ev_join) PK_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     ensure_work(p, 1);
+    // colour offsets on the device and the grid-barrier state of the persistent smoother
+    p->d_fine_off = pool.get<int64_t>(p->fine.off.size());
+    PK_CUDA(cudaMemcpyAsync(p->d_fine_off, p->fine.off.data(), sizeof(int64_t) * p->fine.off.size(),
+                            cudaMemcpyHostToDevice, s));
+    p->d_bar = pool.get<unsigned>(2);
+    p->d_bar_err = pool.get<int>(1);
+    PK_CUDA(cudaMemsetAsync(p->d_bar, 0, sizeof(unsigned) * 2, s));
+    PK_CUDA(cudaMemsetAsync(p->d_bar_err, 0, sizeof(int), s));
     PK_CUDA(cudaStreamSynchronize(s));
     p->have_setup = true;
     autotune(p, s);
@@ -921,6 +1017,7 @@ int solve_device(pkasp_problem *p, const double *b, double *x, int ncols, int64_
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    barrier_status(p, s);
     int status = hs.status[0];
     if (status == ST_RUN) status = PKASP_ENOTCONV;
     if (st) {
@@ -937,6 +1034,8 @@ int solve_device(pkasp_problem *p, const double *b, double *x, int ncols, int64_
     }
     return status;
 }
+
+void check_barrier(pkasp_problem *p, cudaStream_t s) { barrier_status(p, s); }
 
 float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s) {
     if (reps < 1) reps = 1;

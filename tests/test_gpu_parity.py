@@ -205,3 +205,38 @@ def test_fp32_preconditioner(pair, torch_cuda):
     err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
     print(f"fp32-preconditioner solution error vs FP64 oracle: {err:.2e}")
     assert err <= 1e-4
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_persistent_smoother_matches_phase_launches(pair, torch_cuda, prec, lanes):
+    """The whole symmetric sweep in one cooperative launch (grid barriers between colours)
+    adds the same products in the same order as one launch per colour phase: bitwise
+    equal results; and equal to the oracle's SGS."""
+    torch = torch_cuda
+    _, G, O = pair
+    r = torch.tensor(np.random.default_rng(5).standard_normal(G.nh), device="cuda")
+    outs = []
+    for layout in (lanes, -lanes):
+        G.setup(smoother_layout=layout, precond_precision=prec)
+        assert G.info.smoother_layout == layout
+        outs.append(G.apply_smoother(r))
+    assert torch.equal(outs[0], outs[1])
+    if prec == 0:
+        O.setup()
+        _rel_close(outs[1].cpu().numpy(), O.smoother(r.cpu().numpy()), RTOL_OP)
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_persistent_smoother_solve_history(pair, torch_cuda, graph):
+    """PCG with the cooperative-launch smoother (captured in the solve graph or eager)
+    against the oracle: iterations +-1, residual history within 1e-10 ||r_0||."""
+    _, G, O = pair
+    _setup_both(G, O, smoother_layout=-8, use_graph=graph)
+    ref = O.solve()
+    x, st = G.solve(G.rhs(), hist_cap=600)
+    assert st["status"][0] == 0 and abs(st["iters"][0] - ref["iters"]) <= 1
+    h = st["hist"][:, 0]
+    m = min(len(h), len(ref["hist"]))
+    assert (np.abs(h[:m] - ref["hist"][:m]) / ref["hist"][0]).max() <= RTOL_ITER
+    assert np.linalg.norm(x.cpu().numpy() - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
