@@ -344,6 +344,8 @@ def main():
                                  "CSR, lanes per colour" if info64.smoother_layout == -1 else
                                  f"one cooperative launch, CSR x{-info64.smoother_layout} lanes"
                                  if info64.smoother_layout < -1 else
+                                 f"CSR x{info64.smoother_layout - 100} lanes, two rows per lane group"
+                                 if info64.smoother_layout > 100 else
                                  f"CSR x{info64.smoother_layout} lanes"),
              "smoother_ms": smoother_ms,
              "smoother_GBps": smoother_bytes / (smoother_ms / 1e3) / 1e9}

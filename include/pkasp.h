@@ -80,8 +80,10 @@ typedef struct {
     int smoother_layout;  /* fine smoother layout (SGS): 0 = autotuned at setup [0];
                              1 = one launch per colour phase, CSR, lanes fitted per colour;
                              2 = per phase, SELL-32; 4, 8, 16 = per phase, CSR with that
-                             many lanes per row; -4, -8, -16 = the whole symmetric sweep
-                             in one cooperative launch with that many lanes per row.
+                             many lanes per row; 104, 108, 116 = per phase, CSR with 4, 8,
+                             16 lanes and two rows per lane group; -4, -8, -16 = the whole
+                             symmetric sweep in one cooperative launch with that many
+                             lanes per row.
                              spmv_threads != 0 overrides it with its own lane count. */
     int reserved[6];
 } pkasp_options;
@@ -104,8 +106,9 @@ typedef struct {
     int spmv_layout;        /* autotuned layout of the fine SpMV: 0 = SELL-32 (one thread
                                per row), t > 0 = CSR read by t lanes per row */
     int smoother_layout;    /* same for the fine smoother's colour phases; -1 = CSR with
-                               lanes fitted per colour; -t (t > 1) = the whole symmetric
-                               sweep in one cooperative launch, t lanes per row */
+                               lanes fitted per colour; 100 + t = t lanes, two rows per
+                               lane group; -t (t > 1) = the whole symmetric sweep in one
+                               cooperative launch, t lanes per row */
     int block_width;        /* columns of the internal multi-RHS blocks (4, 8, 16, 32, 48
                                or 64) of the last solve with ncols > 1; 0 before one */
     int block_group;        /* columns per group of the multi-RHS fine smoother phases,

@@ -235,6 +235,80 @@ __global__ void __launch_bounds__(kBlock) k_gs_phase(int64_t pb, int64_t pe, con
     if (lead) y[i] = BACK ? own - acc * di : (own - acc) * di;
 }
 
+// The same phase with two rows per sub-warp: rows p and p + half of the colour (no edge
+// joins two rows of one colour, so neither reads the other's result). Both rows' loads
+// are issued before either row's gathers, doubling the loads in flight per lane for
+// phases that are bound by load latency. Each row's sum is formed exactly as above.
+template <int TPR, int NB, typename PT, typename TR, bool BACK>
+__global__ void __launch_bounds__(kBlock) k_gs_phase2(int64_t pb, int64_t pe, const int32_t *__restrict__ perm,
+                                                      const int64_t *__restrict__ xptr,
+                                                      const int32_t *__restrict__ xcol, const PT *__restrict__ xval,
+                                                      const PT *__restrict__ dinv, const TR *r, PT *y) {
+    pdl_trigger();
+    const int64_t half = (pe - pb + 1) / 2;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p0 = pb + gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    int64_t pr[2] = {p0, p0 + half};
+    bool ok[2], lead[2];
+    int32_t i[2];
+    PT di[2];
+    int64_t lo[2], hi[2];
+    int c[2][NB];
+    PT v[2][NB];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        ok[q] = (q == 0 ? pr[0] < pb + half : pr[1] < pe);
+        lead[q] = ok[q] && sub == 0;
+        i[q] = lead[q] ? perm[pr[q]] : 0;
+        di[q] = lead[q] ? dinv[pr[q]] : PT(1);
+        lo[q] = ok[q] ? xptr[pr[q]] : 0;
+        hi[q] = ok[q] ? xptr[pr[q] + 1] : 0;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const int64_t e = lo[q] + sub + (int64_t)k * TPR;
+            const bool in = e < hi[q];
+            c[q][k] = in ? __ldg(&xcol[e]) : -1;
+            v[q][k] = in ? __ldg(&xval[e]) : PT(0);
+        }
+    }
+    pdl_wait();
+    PT own[2], acc[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        own[q] = PT(0);
+        if (lead[q]) own[q] = BACK ? y[i[q]] : (PT)r[i[q]];
+        acc[q] = PT(0);
+    }
+    PT x[2][NB];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < NB; ++k) x[q][k] = c[q][k] >= 0 ? y[c[q][k]] : PT(0);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            if (c[q][k] >= 0) acc[q] += v[q][k] * x[q][k];
+        for (int64_t base = lo[q] + sub + (int64_t)NB * TPR; base < hi[q]; base += (int64_t)NB * TPR) {
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int64_t e = base + (int64_t)k * TPR;
+                const bool in = e < hi[q];
+                c[q][k] = in ? __ldg(&xcol[e]) : -1;
+                v[q][k] = in ? __ldg(&xval[e]) : PT(0);
+            }
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                if (c[q][k] >= 0) acc[q] += v[q][k] * y[c[q][k]];
+        }
+        acc[q] = subwarp_sum<TPR>(acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+        if (lead[q]) y[i[q]] = BACK ? own[q] - acc[q] * di[q] : (own[q] - acc[q]) * di[q];
+}
+
 template <int TPR, typename PT>
 __global__ void __launch_bounds__(kBlock) k_gs_bwd0(int64_t pb, int64_t pe, const int32_t *__restrict__ perm,
                                                     const int64_t *__restrict__ uptr, const int32_t *__restrict__ ucol,

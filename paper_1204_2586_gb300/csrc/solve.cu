@@ -137,8 +137,18 @@ void gs_forward0(const DSplit &sp, int tpr_fixed, const TR *r, PT *y, cudaStream
     for (int c = 0; c < sp.ncol; ++c) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
-        const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(sp.lmax[c]);
+        const bool two = tpr_fixed > 100;  // two rows per sub-warp
+        const int tf = two ? tpr_fixed - 100 : tpr_fixed;
+        const int tpr = tf > 0 ? tf : lanes_for(sp.lmax[c]);
         const int nb = batch_for(tpr, sp.l90[c]);
+        if (two) {
+            PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl(k_gs_phase2<TPR, NB, PT, TR, false>,
+                                                            rows_grid((pe - pb + 1) / 2, TPR), s, pb, pe,
+                                                            (const int32_t *)sp.perm, (const int64_t *)sp.lptr,
+                                                            (const int32_t *)sp.lcol, pick<PT>(sp.lval, sp.lval32),
+                                                            pick<PT>(sp.dinv, sp.dinv32), r, y))));
+            continue;
+        }
         PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl(k_gs_phase<TPR, NB, PT, TR, false>,
                                                         rows_grid(pe - pb, TPR), s, pb, pe,
                                                         (const int32_t *)sp.perm, (const int64_t *)sp.lptr,
@@ -154,8 +164,18 @@ void gs_backward0(const DSplit &sp, int tpr_fixed, PT *y, cudaStream_t s) {
     for (int c = sp.ncol - 2; c >= 0; --c) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
-        const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(sp.umax[c]);
+        const bool two = tpr_fixed > 100;
+        const int tf = two ? tpr_fixed - 100 : tpr_fixed;
+        const int tpr = tf > 0 ? tf : lanes_for(sp.umax[c]);
         const int nb = batch_for(tpr, sp.u90[c]);
+        if (two) {
+            PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl(k_gs_phase2<TPR, NB, PT, PT, true>,
+                                                            rows_grid((pe - pb + 1) / 2, TPR), s, pb, pe,
+                                                            (const int32_t *)sp.perm, (const int64_t *)sp.uptr,
+                                                            (const int32_t *)sp.ucol, pick<PT>(sp.uval, sp.uval32),
+                                                            pick<PT>(sp.dinv, sp.dinv32), (const PT *)y, y))));
+            continue;
+        }
         PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl(k_gs_phase<TPR, NB, PT, PT, true>,
                                                         rows_grid(pe - pb, TPR), s, pb, pe,
                                                         (const int32_t *)sp.perm, (const int64_t *)sp.uptr,
@@ -354,7 +374,8 @@ void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s) 
     // multiplicative: forward GS (or l1 step) from zero, coarse correction of the new
     // residual, backward GS sweep (or l1 step) from the corrected iterate
     const bool jac = p->opt.smoother == PKASP_SMOOTHER_L1JACOBI;
-    const int ts = p->fine_tpr > 0 ? p->fine_tpr : -1;  // the full backward sweep uses the CSR split
+    // the full backward sweep uses the CSR split (one row per lane group)
+    const int ts = p->fine_tpr > 100 ? p->fine_tpr - 100 : p->fine_tpr > 0 ? p->fine_tpr : -1;
     const int ta = p->spmv_tpr;
     PT *t = pickw<PT>(p->w_t, p->w_t32);
     PT *rr = pickw<PT>(p->w_rr, p->w_rr32);
@@ -648,6 +669,7 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
         return;
     }
     // a fixed smoother layout: internal code -1 per-colour lanes, 0 SELL-32, t lanes
+    // 100 + t (t lanes, two rows per sub-warp) passes through
     const int fixed_fine = p->opt.smoother_layout == 1 ? -1 : p->opt.smoother_layout == 2 ? 0
                                                                                            : p->opt.smoother_layout;
     cudaEvent_t e0, e1;
@@ -667,7 +689,8 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
     // only): CSR with the lanes of each colour phase fitted to its longest row
     const int cand_spmv[] = {0, 2, 4, 8};
     // -t < -1: the whole sweep in one cooperative launch with t lanes per row
-    const int cand_fine[] = {-1, 0, 4, 8, 16, -4, -8, -16};
+    // 100 + t: t lanes, two rows per sub-warp
+    const int cand_fine[] = {-1, 0, 4, 8, 16, -4, -8, -16, 104, 108, 116};
     float best = 1e30f;
     int pick_spmv = 0, pick_fine = -1;
     for (int t : cand_spmv) {

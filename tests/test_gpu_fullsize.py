@@ -20,9 +20,10 @@ def fullsize(oracle_mod):
     build.build()
     xyz, t = kuhn_mesh(32, 0.2, 0)
     G = Problem(xyz, t, 3)
-    G.setup(theta=0.25)
+    # bench.py's configuration: l1-Jacobi on the AMG levels
+    G.setup(theta=0.25, level_smoother=1)
     O = oracle_mod.Problem(xyz, t, 3)
-    O.setup(theta=0.25)
+    O.setup(theta=0.25, level_smoother=1)
     yield G, O
     G.close()
 

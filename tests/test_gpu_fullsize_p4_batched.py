@@ -1,0 +1,126 @@
+"""Full-size checks of the two other workloads, in the configurations bench.py and the
+P4 measurement run them:
+
+* P4 on 48^3 jittered Kuhn cubes with kappa = exp(N(0,1)) (6,967,871 unknowns, 513M
+  nonzeros): the operator pattern and sampled rows against the oracle's assembly, the
+  fine colouring bit-exact against the oracle's colouring of the same matrix, and the
+  FP64 and FP32-preconditioner solutions checked on the host against the oracle's own
+  matrix and right-hand side (true residual <= 1e-8, the quantity every solve targets).
+* P2 on 64^3 cubes with 48 right-hand sides (2,048,383 unknowns per column): one column
+  of the blocked solve against the oracle's solve of that column (iterations +-1,
+  history within 1e-10 ||r_0||), and every column of the bench configuration (FP32
+  preconditioner) checked on the host with the oracle's matrix.
+
+The oracle's full P4 solve (80 iterations at ~10 s each on one core) is not run here;
+the residual check against the oracle's operator stands in for it."""
+import numpy as np
+import pytest
+
+from paper_1204_2586_gb300.inputs import kappa_lognormal, kuhn_mesh, rhs_normal
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def p4(oracle_mod):
+    _torch()
+    from paper_1204_2586_gb300 import Problem, build
+
+    build.build()
+    xyz, t = kuhn_mesh(48, 0.2, 0)
+    kap = kappa_lognormal(t.shape[0], 1)
+    G = Problem(xyz, t, 4, kap)
+    O = oracle_mod.Problem(xyz, t, 4, kap)
+    yield G, O
+    G.close()
+
+
+@pytest.mark.slow
+def test_p4_operator_and_colouring(p4, oracle_mod):
+    G, O = p4
+    assert G.nh == 6967871
+    gptr, gcol, gval, _ = G.matrix(0)
+    A = O.matrix(0)
+    assert np.array_equal(gptr, A.ptr) and np.array_equal(gcol, A.col)
+    rows = np.random.default_rng(0).choice(G.nh, 3000, replace=False)
+    for i in rows:
+        lo, hi = A.ptr[i], A.ptr[i + 1]
+        assert np.allclose(gval[lo:hi], A.val[lo:hi], rtol=1e-12, atol=1e-12 * np.abs(A.val[lo:hi]).max())
+    del gptr, gcol, gval
+    bo = O.rhs()
+    assert np.abs(G.rhs().cpu().numpy() - bo).max() <= 1e-12 * np.abs(bo).max()
+    G.setup(level_smoother=1)
+    colour_o, ncol_o = oracle_mod.colour_jp(A, oracle_mod.stream_colour(0, 0))
+    colour_g, ncol_g = G.colours(-1)
+    assert ncol_g == ncol_o and np.array_equal(colour_g, colour_o)
+
+
+@pytest.mark.slow
+def test_p4_solutions_solve_the_oracle_system(p4):
+    torch = _torch()
+    G, O = p4
+    A = O.matrix(0).to_scipy()
+    bo = O.rhs()
+    b = G.rhs()
+    xs = {}
+    for prec in (0, 1):
+        G.setup(level_smoother=1, precond_precision=prec)
+        x, st = G.solve(b, torch.zeros_like(b))
+        assert st["status"][0] == 0 and st["true_rel"][0] <= 1e-8
+        xs[prec] = x.cpu().numpy()
+        rel = np.linalg.norm(bo - A @ xs[prec]) / np.linalg.norm(bo)
+        print(f"P4 48^3 precond {'FP32' if prec else 'FP64'}: {st['iters'][0]} iterations, "
+              f"host true residual {rel:.2e}")
+        assert rel <= 1.05e-8
+    # the FP32 preconditioner changes the iterates, not the solution the CG converges to
+    assert np.linalg.norm(xs[1] - xs[0]) <= 1e-8 * np.linalg.norm(xs[0])
+
+
+@pytest.fixture(scope="module")
+def b48(oracle_mod):
+    _torch()
+    from paper_1204_2586_gb300 import Problem, build
+
+    build.build()
+    xyz, t = kuhn_mesh(64, 0.2, 0)
+    G = Problem(xyz, t, 2)
+    O = oracle_mod.Problem(xyz, t, 2)
+    O.setup(level_smoother=1, flexible=1)
+    yield G, O, rhs_normal(G.nh, 48, 2)
+    G.close()
+
+
+def test_b48_column_against_oracle(b48):
+    torch = _torch()
+    G, O, B = b48
+    assert G.nh == 2048383
+    G.setup(level_smoother=1, flexible=1)
+    x, st = G.solve(torch.tensor(B, device="cuda"), hist_cap=200)
+    ref = O.solve(B[:, 0])
+    assert ref["status"] == 0 and st["status"][0] == 0
+    assert abs(st["iters"][0] - ref["iters"]) <= 1
+    h = st["hist"][:, 0]
+    m = min(st["iters"][0] + 1, len(ref["hist"]))
+    assert (np.abs(h[:m] - ref["hist"][:m]) / ref["hist"][0]).max() <= 1e-10
+    xo = ref["x"]
+    assert np.linalg.norm(x[:, 0].cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+def test_b48_bench_configuration_all_columns(b48):
+    torch = _torch()
+    G, O, B = b48
+    G.setup(theta=0.25, level_smoother=1, precond_precision=1, use_graph=1)
+    x, st = G.solve(torch.tensor(B, device="cuda"))
+    assert st["rc"] == 0 and all(s == 0 for s in st["status"])
+    A = O.matrix(0).to_scipy()
+    R = B - A @ x.cpu().numpy()
+    rel = np.linalg.norm(R, axis=0) / np.linalg.norm(B, axis=0)
+    print(f"48 columns: iterations {min(st['iters'])}-{max(st['iters'])}, host true residual <= {rel.max():.2e}")
+    assert rel.max() <= 1.05e-8

@@ -210,18 +210,19 @@ def test_fp32_preconditioner(pair, torch_cuda):
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("lanes", [4, 8])
 def test_persistent_smoother_matches_phase_launches(pair, torch_cuda, prec, lanes):
-    """The whole symmetric sweep in one cooperative launch (grid barriers between colours)
-    adds the same products in the same order as one launch per colour phase: bitwise
-    equal results; and equal to the oracle's SGS."""
+    """The whole symmetric sweep in one cooperative launch (grid barriers between colours),
+    and the phases with two rows per lane group, add the same products in the same order
+    as one launch per colour phase with one row per group: bitwise equal results; and
+    equal to the oracle's SGS."""
     torch = torch_cuda
     _, G, O = pair
     r = torch.tensor(np.random.default_rng(5).standard_normal(G.nh), device="cuda")
     outs = []
-    for layout in (lanes, -lanes):
+    for layout in (lanes, -lanes, 100 + lanes):
         G.setup(smoother_layout=layout, precond_precision=prec)
         assert G.info.smoother_layout == layout
         outs.append(G.apply_smoother(r))
-    assert torch.equal(outs[0], outs[1])
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
     if prec == 0:
         O.setup()
         _rel_close(outs[1].cpu().numpy(), O.smoother(r.cpu().numpy()), RTOL_OP)
