@@ -198,6 +198,10 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD["name"], choices=[WORKLOAD["name"], BATCHED["name"]])
+    ap.add_argument("--smoother-layout", type=int, default=0,
+                    help="pin the fine smoother layout (pkasp_options.smoother_layout) instead of "
+                         "autotuning it; for profiler runs, under which the autotuner's timings "
+                         "are distorted")
     ap.add_argument("--mesh-n", type=int, default=0,
                     help="cubes per side of the mesh instead of the workload's own (a smaller case "
                          "of the same kernels for profiler captures; the JSON line states the size)")
@@ -234,7 +238,8 @@ def main():
     torch.cuda.synchronize()
     assemble_s = time.perf_counter() - t_as
     t_su = time.perf_counter()
-    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, use_graph=0 if args.eager else 1)
+    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, use_graph=0 if args.eager else 1,
+            smoother_layout=args.smoother_layout)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_su
     b = G.rhs()

@@ -675,8 +675,7 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
     cudaEvent_t e0, e1;
     PK_CUDA(cudaEventCreate(&e0));
     PK_CUDA(cudaEventCreate(&e1));
-    auto timed = [&](auto fn) {
-        fn();
+    auto time3 = [&](auto fn) {  // three back-to-back runs
         PK_CUDA(cudaEventRecord(e0, s));
         for (int i = 0; i < 3; ++i) fn();
         PK_CUDA(cudaEventRecord(e1, s));
@@ -685,37 +684,42 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
         cudaEventElapsedTime(&ms, e0, e1);
         return ms;
     };
+    // Candidates are timed round-robin, three rounds, best round per candidate: the
+    // GPU's clock can still be ramping up during setup, and timing candidates one after
+    // another would favour the later ones.
+    auto tune = [&](const int *cand, int nc, int *slot, auto run) {
+        std::vector<float> best(nc, 1e30f);
+        for (int k = 0; k < nc; ++k) {
+            *slot = cand[k];
+            run();  // warm-up (first use of each variant)
+        }
+        for (int round = 0; round < 3; ++round)
+            for (int k = 0; k < nc; ++k) {
+                *slot = cand[k];
+                best[k] = std::min(best[k], time3(run));
+            }
+        int pick = 0;
+        for (int k = 1; k < nc; ++k)
+            if (best[k] < best[pick]) pick = k;
+        return cand[pick];
+    };
     // 0: SELL-32, one thread per row; t > 0: CSR with t lanes per row; -1 (smoother
     // only): CSR with the lanes of each colour phase fitted to its longest row
     const int cand_spmv[] = {0, 2, 4, 8};
-    // -t < -1: the whole sweep in one cooperative launch with t lanes per row
-    // 100 + t: t lanes, two rows per sub-warp
-    const int cand_fine[] = {-1, 0, 4, 8, 16, -4, -8, -16, 104, 108, 116};
-    float best = 1e30f;
-    int pick_spmv = 0, pick_fine = -1;
-    for (int t : cand_spmv) {
-        p->spmv_tpr = t;
-        float ms = timed([&] { spmv_fine(p, p->d_b, p->w_q, s); });
-        if (ms < best) best = ms, pick_spmv = t;
-    }
-    best = 1e30f;
+    // 100 + t: t lanes, two rows per sub-warp. The one-launch cooperative sweep (-t) is
+    // not a candidate: its grid barrier cost more than a phase launch on every measured
+    // problem (P3 32^3, P4 48^3); smoother_layout selects it explicitly.
+    const int cand_fine[] = {-1, 0, 4, 8, 16, 104, 108, 116};
+    const int pick_spmv = tune(cand_spmv, 4, &p->spmv_tpr, [&] { spmv_fine(p, p->d_b, p->w_q, s); });
+    p->spmv_tpr = pick_spmv;
+    int pick_fine = -1;
     if (p->opt.smoother == PKASP_SMOOTHER_SGS && p->opt.smoother_layout != 0) {
         pick_fine = fixed_fine;
     } else if (p->opt.smoother == PKASP_SMOOTHER_SGS) {
-        for (int t : cand_fine) {
-            p->fine_tpr = t;
-            float ms = (p->opt.precond_precision == PKASP_PREC_FP32)
-                           ? timed([&] { smoother<float>(p, p->d_b, p->w_zs32, s); })
-                           : timed([&] { smoother<double>(p, p->d_b, p->w_zs, s); });
-            if (t < -1) {
-                try {
-                    barrier_status(p, s);
-                } catch (const Error &) {
-                    continue;  // a candidate whose barrier gave up is not taken
-                }
-            }
-            if (ms < best) best = ms, pick_fine = t;
-        }
+        if (p->opt.precond_precision == PKASP_PREC_FP32)
+            pick_fine = tune(cand_fine, 8, &p->fine_tpr, [&] { smoother<float>(p, p->d_b, p->w_zs32, s); });
+        else
+            pick_fine = tune(cand_fine, 8, &p->fine_tpr, [&] { smoother<double>(p, p->d_b, p->w_zs, s); });
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
