@@ -45,6 +45,20 @@ CONFIG = {
     "l2_flush": "inputs larger than L2: A_h alone is 480 MB (12 B/nnz x 39,951,635 nnz) vs 129 MB L2",
     "parallelism": "replicas (one independent solve per GPU)",
 }
+P4 = dict(name="p4_n48_lognormal", k=4, n=48, jitter=0.2, mesh_seed=0, kappa_seed=1)
+CONFIG_P4 = {
+    "workload": "P4 Poisson, kappa_e = exp(N(0,1)) per tet (seed 1), 48^3 jittered Kuhn cubes (663,552 tets, "
+                "6,967,871 unknowns, 512,842,207 nonzeros), sine source, PCG to rel. residual 1e-8, "
+                "additive aux-space preconditioner (1 SGS sweep + 1 P1 AMG V-cycle, theta=0.25, l1-Jacobi "
+                "levels); value: FP64 throughout; the mixed-precision solve (FP32 preconditioner, FP64 "
+                "flexible CG) is reported beside it",
+    "mesh": "unit cube, 48^3 cubes x 6 Kuhn tets, interior vertices jittered by <=0.2h (seed 0)",
+    "k": 4,
+    "n_h": 6967871,
+    "l2_flush": "inputs larger than L2: A_h alone is 6.2 GB vs 129 MB L2",
+    "parallelism": "replicas (one independent solve per GPU)",
+}
+SINGLE = {WORKLOAD["name"]: (WORKLOAD, CONFIG), P4["name"]: (P4, CONFIG_P4)}
 BATCHED = dict(name="p2_n64_batched48", k=2, n=64, jitter=0.2, mesh_seed=0, rhs_seed=2, ncols=48)
 CONFIG_BATCHED = {
     "workload": "P2 vector Laplacian (3 components x 16 right-hand sides = 48 columns of the scalar "
@@ -63,6 +77,7 @@ CONFIG_BATCHED = {
 # per clock per SM (2 FP64 FMA per clock per SM) = 1.259 TFLOP/s (nominal 1.25)
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 ORACLE_SAMPLE_ITERS = 12
+NOMINAL_HBM_GBS = 8000.0  # GB300's nominal HBM3e bandwidth, for the second fraction
 # AMG level smoother: l1-Jacobi (1), one kernel per smoothing step; multicolour GS on the
 # dense coarse levels needs one launch per colour and costs ~25x more per V-cycle here
 LEVEL_SMOOTHER = 1
@@ -131,12 +146,18 @@ def dist_env():
     return ws, rank, local
 
 
+def workload_kappa(wl, nt):
+    from paper_1204_2586_gb300.inputs import kappa_lognormal
+
+    return kappa_lognormal(nt, wl["kappa_seed"]) if wl.get("kappa_seed") is not None else None
+
+
 def make_problem():
     from paper_1204_2586_gb300 import Problem
     from paper_1204_2586_gb300.inputs import kuhn_mesh
 
     xyz, t = kuhn_mesh(WORKLOAD["n"], WORKLOAD["jitter"], WORKLOAD["mesh_seed"])
-    return xyz, t, Problem(xyz, t, WORKLOAD["k"])
+    return xyz, t, Problem(xyz, t, WORKLOAD["k"], workload_kappa(WORKLOAD, t.shape[0]))
 
 
 def run_cpu_oracle(steps, warmup, sample_iters=ORACLE_SAMPLE_ITERS, batched=False, mesh_n=0):
@@ -150,7 +171,7 @@ def run_cpu_oracle(steps, warmup, sample_iters=ORACLE_SAMPLE_ITERS, batched=Fals
     if mesh_n:
         wl["n"] = mesh_n
     xyz, t = kuhn_mesh(wl["n"], wl["jitter"], wl["mesh_seed"])
-    P = oracle.Problem(xyz, t, wl["k"])
+    P = oracle.Problem(xyz, t, wl["k"], workload_kappa(wl, t.shape[0]))
     if batched:
         P.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, max_iter=sample_iters, flexible=1)
         b = rhs_normal(P.nh, 1, wl["rhs_seed"])[:, 0]
@@ -179,25 +200,27 @@ def reference_arm(args):
     if ws > 1 and rank != 0:
         return
     batched = args.workload == BATCHED["name"]
-    value, cpu = run_cpu_oracle(args.steps, args.warmup, sample_iters=4, batched=batched)
+    sample = 2 if args.workload == P4["name"] else 4
+    value, cpu = run_cpu_oracle(args.steps, args.warmup, sample_iters=sample, batched=batched)
     ms = cpu["seconds"] / args.steps * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": CONFIG_BATCHED if batched else CONFIG,
+            "config": CONFIG_BATCHED if batched else SINGLE[args.workload][1],
             "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 def main():
+    global WORKLOAD, CONFIG
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD["name"], choices=[WORKLOAD["name"], BATCHED["name"]])
+    ap.add_argument("--workload", default=WORKLOAD["name"], choices=[WORKLOAD["name"], P4["name"], BATCHED["name"]])
     ap.add_argument("--smoother-layout", type=int, default=0,
                     help="pin the fine smoother layout (pkasp_options.smoother_layout) instead of "
                          "autotuning it; for profiler runs, under which the autotuner's timings "
@@ -213,6 +236,8 @@ def main():
         ap.error("--mesh-n applies to the multi-RHS workload only")
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload in SINGLE:
+        WORKLOAD, CONFIG = SINGLE[args.workload]
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -317,17 +342,21 @@ def main():
     peak = hbm if hbm else 6800.0
     src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback"
     s_ach = smoother_bytes / (smoother_ms / 1e3) / 1e9
+    p3 = WORKLOAD["name"] == "p3_n32"
     roof = {"bound": "hbm", "kernel": "k_gs_phase (colour phases of the fine SGS S_k, FP64)",
             "achieved": s_ach, "peak": peak, "unit": "GB/s", "frac": s_ach / peak, "traffic": None,
+            "frac_of_nominal_8000": s_ach / NOMINAL_HBM_GBS,
             "peak_source": src, "bytes_per_application": smoother_bytes, "ms_per_application": smoother_ms,
             "phases_per_application": 2 * int(info64.fine_colours) - 1,
-            "note": "FP64-pipe bound per phase (ncu: fp64 pipe 71% busy while active); "
+            "note": "latency per phase plus the FP64 pipe (ncu: fp64 pipe 51-57% busy while active); "
                     "see profiles/k_gs_phase_p3_n32.md"}
     achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
     roof_spmv = {"bound": "hbm", "kernel": "k_spmv_pq / k_sell_spmv (fine SpMV, SELL-32, FP64)",
                  "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                 "traffic": 552.3e6 + 8.1e6, "traffic_source":
-                 "ncu dram__bytes_read+write of one k_spmv_pq launch, profiles/k_spmv_pq_sell_p3_n32.md",
+                 "frac_of_nominal_8000": achieved / NOMINAL_HBM_GBS,
+                 "traffic": 552.3e6 + 8.1e6 if p3 else None, "traffic_source":
+                 "ncu dram__bytes_read+write of one k_spmv_pq launch, profiles/k_spmv_pq_sell_p3_n32.md"
+                 if p3 else None,
                  "peak_source": src, "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms}
     # the mixed-precision variant of the same solve: FP32 smoother / I_P / AMG, FP64 flexible CG
     G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, precond_precision=1, use_graph=0 if args.eager else 1)
@@ -359,7 +388,7 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            _, cpu = run_cpu_oracle(1, 0)
+            _, cpu = run_cpu_oracle(1, 0, sample_iters=ORACLE_SAMPLE_ITERS if p3 else 2)
             cpu.pop("seconds", None)
         except Exception as e:  # the baseline must not sink the GPU line
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
@@ -486,6 +515,7 @@ def run_batched(args, ws, rank, local):
     roof_sm = {"bound": "hbm", "kernel": "kb_gs_phase<*, float> (blocked FP32 fine SGS)",
                "achieved": sm_bytes / (sm_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                "frac": sm_bytes / (sm_ms / 1e3) / 1e9 / hbm, "traffic": None,
+               "frac_of_nominal_8000": sm_bytes / (sm_ms / 1e3) / 1e9 / NOMINAL_HBM_GBS,
                "ms_per_application": sm_ms, "bytes_per_application": sm_bytes,
                "column_group": layout[1], "lanes_per_row": layout[2]}
     prec_ms = G.time_kernel(6, 5)
