@@ -39,7 +39,8 @@ class OOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("mode", C.c_int), ("smoother", C.c_int),
                 ("level_smoother", C.c_int), ("coarse_size", C.c_int),
                 ("max_levels", C.c_int), ("seed", C.c_uint64), ("tol", C.c_double),
-                ("max_iter", C.c_int), ("flexible", C.c_int)]
+                ("max_iter", C.c_int), ("flexible", C.c_int), ("krylov", C.c_int),
+                ("restart", C.c_int)]
 
 
 def lib():
@@ -278,7 +279,7 @@ SOURCE_NONE, SOURCE_SINE = 0, 1
 
 def default_opts(**kw) -> OOpts:
     o = OOpts(theta=0.25, mode=0, smoother=0, level_smoother=0, coarse_size=256,
-              max_levels=25, seed=0, tol=1e-8, max_iter=500, flexible=0)
+              max_levels=25, seed=0, tol=1e-8, max_iter=500, flexible=0, krylov=0, restart=30)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

@@ -1596,8 +1596,128 @@ void orc_apply_prec(oproblem *P, const double *r, double *z) {
  *     uses beta = (z_new, r_new - r_old) / (z_old, r_old).
  *     Returns 0 converged, 1 not converged in max_iter, 2 breakdown (p^T A p <= 0).
  * ---------------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------------------
+ * 12b. FGMRES(m): the outer iteration of the paper's experiments (Sec. 6.2), Saad's
+ *      flexible GMRES with right preconditioning.
+ *        r0 = b - A x0, beta = ||r0||, v_1 = r0 / beta, g = beta e_1
+ *        for j = 1..m:  z_j = B v_j;  w = A z_j;
+ *                       h_ij = (w, v_i) and w -= sum_i h_ij v_i for i <= j, twice
+ *                       (classical Gram-Schmidt with one reorthogonalisation; the
+ *                       second pass's coefficients are added to h_ij);
+ *                       h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j};
+ *                       rotate column j of H by the earlier Givens rotations, choose
+ *                       the rotation that zeroes h_{j+1,j}, apply it to g;
+ *                       |g_{j+1}| = ||b - A x_j|| (in exact arithmetic); stop when it is
+ *                       <= tol ||b - A x_initial|| or at max_iter total steps
+ *        y = H(1:k,1:k)^{-1} g(1:k) (upper triangular), x += sum_j y_j z_j
+ *      then restart from the true residual until converged. A zero h_{j+1,j} ends the
+ *      cycle (the Krylov space holds the solution).
+ * ---------------------------------------------------------------------------------- */
+int orc_fgmres(oproblem *P, const double *b, double *x, double *hist, int hist_cap,
+               int *iters_out, double *true_rel_out) {
+    const int64_t n = P->nh;
+    const int m = P->o.restart > 0 ? P->o.restart : 30;
+    double *V = (double *)xmalloc(sizeof(double) * (size_t)n * (size_t)(m + 1));
+    double *Z = (double *)xmalloc(sizeof(double) * (size_t)n * (size_t)m);
+    double *w = (double *)xmalloc(sizeof(double) * (size_t)n);
+    double *H = (double *)xmalloc(sizeof(double) * (size_t)(m + 1) * (size_t)m); /* H[i*m + j] */
+    double *cs = (double *)xmalloc(sizeof(double) * (size_t)m);
+    double *sn = (double *)xmalloc(sizeof(double) * (size_t)m);
+    double *g = (double *)xmalloc(sizeof(double) * (size_t)(m + 1));
+    double *y = (double *)xmalloc(sizeof(double) * (size_t)m);
+    double *hc = (double *)xmalloc(sizeof(double) * (size_t)(m + 1));
+    int it = 0, status = 1;
+    orc_spmv(P->Ah, x, w);
+    for (int64_t i = 0; i < n; ++i) V[i] = b[i] - w[i];
+    const double r0 = sqrt(dot(n, V, V));
+    if (hist && hist_cap > 0) hist[0] = r0;
+    double beta = r0;
+    if (r0 == 0.0) status = 0;
+    while (status == 1) {
+        for (int64_t i = 0; i < n; ++i) V[i] /= beta;
+        for (int i = 0; i <= m; ++i) g[i] = 0.0;
+        g[0] = beta;
+        int k = 0; /* Arnoldi steps of this cycle */
+        int converged = 0;
+        for (int j = 0; j < m && it < P->o.max_iter; ++j) {
+            double *vj = V + (size_t)j * (size_t)n, *zj = Z + (size_t)j * (size_t)n;
+            orc_apply_prec(P, vj, zj);
+            orc_spmv(P->Ah, zj, w);
+            for (int i = 0; i <= j; ++i) H[i * m + j] = 0.0;
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int i = 0; i <= j; ++i) hc[i] = dot(n, w, V + (size_t)i * (size_t)n);
+                for (int i = 0; i <= j; ++i) {
+                    const double *vi = V + (size_t)i * (size_t)n;
+                    for (int64_t q = 0; q < n; ++q) w[q] -= hc[i] * vi[q];
+                    H[i * m + j] += hc[i];
+                }
+            }
+            const double hn = sqrt(dot(n, w, w));
+            H[(j + 1) * m + j] = hn;
+            double *vn = V + (size_t)(j + 1) * (size_t)n;
+            if (hn > 0.0)
+                for (int64_t q = 0; q < n; ++q) vn[q] = w[q] / hn;
+            /* earlier rotations on column j, then the new one */
+            for (int i = 0; i < j; ++i) {
+                const double a = H[i * m + j], c = H[(i + 1) * m + j];
+                H[i * m + j] = cs[i] * a + sn[i] * c;
+                H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            const double a = H[j * m + j], c = H[(j + 1) * m + j];
+            const double d = sqrt(a * a + c * c);
+            cs[j] = d > 0.0 ? a / d : 1.0;
+            sn[j] = d > 0.0 ? c / d : 0.0;
+            H[j * m + j] = d;
+            H[(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++it;
+            k = j + 1;
+            const double est = fabs(g[j + 1]);
+            if (hist && it < hist_cap) hist[it] = est;
+            if (est <= P->o.tol * r0 || hn == 0.0) {
+                converged = 1;
+                break;
+            }
+        }
+        /* x += Z y with H(1:k,1:k) y = g(1:k) */
+        for (int i = k - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * y[l];
+            y[i] = s / H[i * m + i];
+        }
+        for (int l = 0; l < k; ++l) {
+            const double *zl = Z + (size_t)l * (size_t)n;
+            for (int64_t q = 0; q < n; ++q) x[q] += y[l] * zl[q];
+        }
+        /* restart from the true residual */
+        orc_spmv(P->Ah, x, w);
+        for (int64_t i = 0; i < n; ++i) V[i] = b[i] - w[i];
+        beta = sqrt(dot(n, V, V));
+        if (beta <= P->o.tol * r0) {
+            status = 0;
+            break;
+        }
+        if (it >= P->o.max_iter) break;
+        (void)converged;
+    }
+    if (true_rel_out) *true_rel_out = r0 > 0.0 ? beta / r0 : 0.0;
+    if (iters_out) *iters_out = it;
+    free(V);
+    free(Z);
+    free(w);
+    free(H);
+    free(cs);
+    free(sn);
+    free(g);
+    free(y);
+    free(hc);
+    return status;
+}
+
 int orc_solve(oproblem *P, const double *b, double *x, double *hist, int hist_cap,
               int *iters_out, double *true_rel_out) {
+    if (P->o.krylov == 1) return orc_fgmres(P, b, x, hist, hist_cap, iters_out, true_rel_out);
     int64_t n = P->nh;
     double *r = (double *)xmalloc(sizeof(double) * (size_t)n);
     double *z = (double *)xmalloc(sizeof(double) * (size_t)n);

@@ -25,6 +25,8 @@ typedef struct {
     double tol;          /* relative residual target */
     int max_iter;
     int flexible;        /* 1: flexible CG beta */
+    int krylov;          /* outer iteration: 0 CG (FCG when flexible), 1 FGMRES (Sec. 6.2) */
+    int restart;         /* FGMRES restart length m */
 } oopts;
 
 /* problem construction */
@@ -77,6 +79,12 @@ void orc_fine_colour(const oproblem *p, int32_t *colour);
 void orc_apply_prec(oproblem *p, const double *r, double *z);
 void orc_vcycle(oproblem *p, const double *b, double *x);
 void orc_smoother(oproblem *p, const double *r, double *z);
+/* FGMRES(m) (Saad's flexible GMRES, right preconditioning by orc_apply_prec), classical
+ * Gram-Schmidt applied twice per Arnoldi step; hist[k] = the least-squares residual
+ * estimate after k inner steps (hist[0] = ||b - A x0||). Called by orc_solve when
+ * krylov = 1. */
+int orc_fgmres(oproblem *p, const double *b, double *x, double *hist, int hist_cap,
+               int *iters_out, double *true_rel_out);
 int orc_solve(oproblem *p, const double *b, double *x, double *hist, int hist_cap,
               int *iters_out, double *true_rel_out);
 void orc_grad_kappa(const oproblem *p, const double *u, const double *lam, double *g);

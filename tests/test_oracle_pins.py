@@ -477,6 +477,82 @@ def test_fcg_matches_pcg_with_fixed_preconditioner(oracle_mod):
     assert np.allclose(a["hist"], b["hist"], rtol=1e-6)
 
 
+# ---------------------------------------------------------------------------------
+# FGMRES (the outer iteration of Sec. 6.2)
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fgmres_minimal_residual_over_explicit_krylov_space(oracle_mod, mode):
+    """With a fixed preconditioner B, FGMRES is right-preconditioned GMRES: after k steps
+    ||b - A x_k|| is the minimum of ||r_0 - A B K c|| over c, K = [r_0, ABr_0, ...,
+    (AB)^{k-1} r_0]. The oracle's residual estimates must equal that minimum computed by
+    dense least squares on the explicit Krylov matrix (B assembled column by column)."""
+    xyz, t = _mesh(3)
+    P = oracle_mod.Problem(xyz, t, 2, kappa_lognormal(t.shape[0], 1))
+    P.setup(mode=mode, coarse_size=8, krylov=1, restart=30, tol=1e-14, max_iter=8)
+    A = P.matrix(0).to_scipy().toarray()
+    n = A.shape[0]
+    B = np.column_stack([P.apply_prec(np.eye(n)[:, j]) for j in range(n)])
+    b = P.rhs()
+    out = P.solve(b)
+    AB = A @ B
+    K = [b / np.linalg.norm(b)]
+    for _ in range(7):
+        v = AB @ K[-1]
+        K.append(v / np.linalg.norm(v))
+    for k in range(1, 8):
+        Kk = np.column_stack(K[:k])
+        c, *_ = np.linalg.lstsq(AB @ Kk, b, rcond=None)
+        rmin = np.linalg.norm(b - AB @ Kk @ c)
+        assert abs(out["hist"][k] - rmin) <= 1e-7 * np.linalg.norm(b), (k, out["hist"][k], rmin)
+    # and the history is non-increasing (minimal residual over nested spaces)
+    assert np.all(np.diff(out["hist"][: out["iters"] + 1]) <= 1e-14 * np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("k_stop", [3, 7])
+def test_fgmres_estimate_is_the_true_residual(oracle_mod, k_stop):
+    """|g_{k+1}| of the Givens-rotated least-squares problem is ||b - A x_k|| for the
+    x_k that the cycle's triangular solve produces: stop after k steps and compare with
+    the true residual of the returned x."""
+    xyz, t = _mesh(4)
+    P = oracle_mod.Problem(xyz, t, 3)
+    P.setup(krylov=1, restart=30, max_iter=k_stop)
+    out = P.solve()
+    assert out["iters"] == k_stop and out["status"] != 0
+    r0 = out["hist"][0]
+    assert abs(out["true_rel"] * r0 - out["hist"][k_stop]) <= 1e-9 * r0
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_fgmres_reaches_dense_solution_with_restarts(oracle_mod, k):
+    xyz, t = _mesh(3)
+    P = oracle_mod.Problem(xyz, t, k, kappa_lognormal(t.shape[0], 1))
+    A = P.matrix(0).to_scipy().toarray()
+    u = np.linalg.solve(A, P.rhs())
+    iters = {}
+    for m in (30, 3):
+        P.setup(krylov=1, restart=m, tol=1e-12, max_iter=400)
+        out = P.solve()
+        assert out["status"] == 0 and out["true_rel"] <= 1e-12 * 1.01
+        assert np.linalg.norm(out["x"] - u) <= 1e-9 * np.linalg.norm(u)
+        iters[m] = out["iters"]
+    # restarting throws the Krylov space away: never fewer steps
+    assert iters[3] >= iters[30]
+
+
+def test_fgmres_multiplicative_mode_iterations_flat_in_h(oracle_mod):
+    """The paper's setting (Sec. 6.2: FGMRES, one multilevel cycle, Algorithm 2.1 with
+    pre-smoothing): iteration counts stay flat as h halves (Theorem 4.2)."""
+    its = []
+    for n in (4, 8):
+        xyz, t = _mesh(n)
+        P = oracle_mod.Problem(xyz, t, 2)
+        P.setup(mode=1, krylov=1, tol=1e-6)
+        out = P.solve()
+        assert out["status"] == 0
+        its.append(out["iters"])
+    assert its[1] <= its[0] + 2, its
+
+
 @pytest.mark.slow
 def test_iterations_independent_of_h(oracle_mod):
     """Theorem 4.2: the two-level convergence rate is bounded independently of h."""
