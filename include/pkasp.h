@@ -52,6 +52,7 @@ enum {
 enum { PKASP_MODE_ADDITIVE = 0, PKASP_MODE_MULTIPLICATIVE = 1 };
 enum { PKASP_SMOOTHER_SGS = 0, PKASP_SMOOTHER_L1JACOBI = 1 };
 enum { PKASP_PREC_FP64 = 0, PKASP_PREC_FP32 = 1 };
+enum { PKASP_KRYLOV_CG = 0, PKASP_KRYLOV_FGMRES = 1 };
 enum { PKASP_SOURCE_NONE = 0, PKASP_SOURCE_SINE = 1 };
 enum { PKASP_MAX_LEVELS = 25, PKASP_MAX_COLS = 64 };
 
@@ -85,7 +86,12 @@ typedef struct {
                              symmetric sweep in one cooperative launch with that many
                              lanes per row.
                              spmv_threads != 0 overrides it with its own lane count. */
-    int reserved[6];
+    int krylov;           /* outer iteration: PKASP_KRYLOV_CG (CG; flexible CG with the FP32
+                             preconditioner) or PKASP_KRYLOV_FGMRES (Saad's flexible GMRES with
+                             right preconditioning, the outer method of Sec. 6.2; one
+                             right-hand side per call) [CG] */
+    int restart;          /* FGMRES restart length m, 1..256 [30] */
+    int reserved[4];
 } pkasp_options;
 
 /* Problem sizes after assembly and (for the AMG entries) after setup. */

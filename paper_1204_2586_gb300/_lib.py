@@ -19,6 +19,7 @@ ERROR_NAMES = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: 
 MODE_ADDITIVE, MODE_MULTIPLICATIVE = 0, 1
 SMOOTHER_SGS, SMOOTHER_L1JACOBI = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
+KRYLOV_CG, KRYLOV_FGMRES = 0, 1
 SOURCE_NONE, SOURCE_SINE = 0, 1
 MAX_LEVELS, MAX_COLS = 25, 64
 
@@ -28,7 +29,8 @@ class pkasp_options(C.Structure):
                 ("level_smoother", C.c_int), ("coarse_size", C.c_int), ("max_levels", C.c_int),
                 ("seed", C.c_uint64), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("flexible", C.c_int), ("precond_precision", C.c_int), ("use_graph", C.c_int),
-                ("spmv_threads", C.c_int), ("smoother_layout", C.c_int), ("reserved", C.c_int * 6)]
+                ("spmv_threads", C.c_int), ("smoother_layout", C.c_int), ("krylov", C.c_int),
+                ("restart", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class pkasp_info(C.Structure):

@@ -106,6 +106,8 @@ struct Level {
     float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr;
 };
 
+struct GmresState;  // gmres.cu
+
 // Scalars of one PCG run (device), per column.
 struct PcgState {
     double rho[PKASP_MAX_COLS];
@@ -213,6 +215,19 @@ struct pkasp_problem {
     cudaGraphExec_t bgraph_exec = nullptr;
     cudaGraph_t bgraph = nullptr;
     long long bg_init = 0, bg_body = 0, bg_final = 0;
+    // FGMRES(m) (gmres.cu): Arnoldi vectors V [(m+1)][n], preconditioned vectors Z [m][n]
+    pk::DevPool gm_pool;
+    int gm_m = 0;
+    double *gm_V = nullptr, *gm_Z = nullptr, *gm_w = nullptr, *gm_vin = nullptr, *gm_zout = nullptr;
+    double *gm_H = nullptr, *gm_g = nullptr, *gm_cs = nullptr, *gm_sn = nullptr, *gm_y = nullptr,
+           *gm_hc = nullptr, *gm_part = nullptr;
+    unsigned *gm_cnt = nullptr;
+    pk::GmresState *gm_state = nullptr;
+    cudaGraphExec_t gm_graph_exec = nullptr;
+    cudaGraph_t gm_graph = nullptr;
+    const void *gm_key_b = nullptr;
+    void *gm_key_x = nullptr;
+    long long gm_g_init = 0, gm_g_body = 0;
     // staging of host arrays [n][ld]
     pk::DevPool stage_pool;
     int64_t stage_elems = 0;
@@ -268,6 +283,9 @@ int solve_batched(pkasp_problem *p, const double *b, double *x, int ncols, int64
                   cudaStream_t s);
 void free_batched(pkasp_problem *p);
 float time_batched(pkasp_problem *p, int which, int reps, cudaStream_t s);
+// FGMRES(m) outer iteration (gmres.cu); b and x device vectors [n_h]
+int solve_gmres(pkasp_problem *p, const double *b, double *x, pkasp_stats *st, cudaStream_t s);
+void free_gmres(pkasp_problem *p);
 float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s);
 
 // SELL-32 builders (sell.cu)

@@ -14,6 +14,7 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include "persist.cuh"
+#include "rowop.cuh"
 
 namespace pk {
 
@@ -437,46 +438,6 @@ __global__ void k_state_restart(PcgState *st) {
     st->loops = 0;
 }
 
-// The fine operator A_h as the fused PCG kernels see it: CSR rows read by sub-warps of
-// TPR lanes (TPR > 0), or SELL-32 slices read one thread per row (TPR == 0; ptr then
-// holds the slice pointers and sw the slice widths).
-struct RowOp {
-    const int64_t *ptr;
-    const int32_t *col;
-    const double *val;
-    const int32_t *sw;
-};
-
-RowOp fine_op(const pkasp_problem *p) {
-    if (p->spmv_tpr == 0) return RowOp{p->Asell.sptr, p->Asell.col, p->Asell.val, p->Asell.swidth};
-    return RowOp{p->Ah.ptr, p->Ah.col, p->Ah.val, nullptr};
-}
-
-// f(row, (A x)_row) for every row, grid-stride; every lane of a warp runs the same
-// number of trips (the shuffles of the CSR form need the whole warp)
-template <int TPR, class F>
-__device__ __forceinline__ void for_rows(int64_t n, const RowOp &A, const double *x, F f) {
-    if constexpr (TPR == 0) {
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += stride) {
-            const int64_t s = row >> 5;
-            f(row, sell_dot<double>(A.ptr[s] + (row & 31), A.sw[s], A.col, A.val, x));
-        }
-    } else {
-        const int sub = threadIdx.x & (TPR - 1);
-        const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-        const int rpw = 32 / TPR, sg = (threadIdx.x & 31) / TPR;
-        for (int64_t base = warp * rpw; base < n; base += nwarps * rpw) {
-            const int64_t row = base + sg;
-            const bool ok = row < n;
-            int64_t lo = ok ? A.ptr[row] : 0, hi = ok ? A.ptr[row + 1] : 0;
-            double s = row_dot<TPR, double>(lo, hi, sub, A.col, A.val, x);
-            if (ok && sub == 0) f(row, s);
-        }
-    }
-}
-
 // r = b - A x, ||r||; on the first start also r0 and hist[0]
 template <int TPR>
 __global__ void __launch_bounds__(kBlock) k_init_residual(int64_t n, RowOp A, const double *__restrict__ b,
@@ -636,6 +597,7 @@ __global__ void __launch_bounds__(kBlock) k_true_residual(int64_t n, RowOp A, co
 // ---------------------------------------------------------------------------------
 void free_setup(pkasp_problem *p) {
     free_batched(p);
+    free_gmres(p);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     p->graph_exec = nullptr;
@@ -887,16 +849,6 @@ void apply_vcycle(pkasp_problem *p, const double *b, double *x, cudaStream_t s) 
 
 namespace {
 
-#define PK_FMT_SWITCH(tpr, BODY)                          \
-    switch (tpr) {                                        \
-        case 0: { constexpr int TPR = 0; BODY; } break;   \
-        case 2: { constexpr int TPR = 2; BODY; } break;   \
-        case 4: { constexpr int TPR = 4; BODY; } break;   \
-        case 8: { constexpr int TPR = 8; BODY; } break;   \
-        case 16: { constexpr int TPR = 16; BODY; } break; \
-        default: { constexpr int TPR = 32; BODY; } break; \
-    }
-
 void enqueue_init(pkasp_problem *p, const double *b, double *x, cudaStream_t s) {
     const int tpr = p->spmv_tpr;
     const RowOp A = fine_op(p);
@@ -983,6 +935,10 @@ void build_graph(pkasp_problem *p, const double *b, double *x) {
 
 int solve_device(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld, pkasp_stats *st,
                  cudaStream_t s) {
+    if (p->opt.krylov == PKASP_KRYLOV_FGMRES) {
+        if (ncols != 1 || ld != 1) fail(PKASP_EINVAL, "FGMRES solves one right-hand side per call");
+        return solve_gmres(p, b, x, st, s);
+    }
     if (ncols != 1 || ld != 1) return solve_batched(p, b, x, ncols, ld, st, s);
     ensure_work(p, 1);
     const int cap = (st && st->hist_cap > 0) ? st->hist_cap : 1;

@@ -1,0 +1,129 @@
+"""GPU parity of FGMRES(m) (the outer iteration of Sec. 6.2) against the oracle's
+FGMRES: residual estimates per step within 1e-10 ||r_0||, step counts +-1, solutions
+within 1e-8, for both preconditioner forms, with and without restarts, graph and eager."""
+import numpy as np
+import pytest
+
+from paper_1204_2586_gb300.inputs import kappa_lognormal, kuhn_mesh, rhs_normal
+
+pytestmark = pytest.mark.gpu
+
+RTOL_ITER = 1e-10
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1204_2586_gb300 import build
+
+    build.build()
+    return torch
+
+
+CASES = {"p2_n8": (2, 8, None), "p3_n5_lognormal": (3, 5, 1), "p4_n3_lognormal": (4, 3, 1)}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def pair(request, torch_cuda, oracle_mod):
+    from paper_1204_2586_gb300 import Problem
+
+    k, n, ks = CASES[request.param]
+    xyz, t = kuhn_mesh(n, 0.2, 0)
+    kap = np.ones(t.shape[0]) if ks is None else kappa_lognormal(t.shape[0], ks)
+    G = Problem(xyz, t, k, kap)
+    O = oracle_mod.Problem(xyz, t, k, kap)
+    yield request.param, G, O
+    G.close()
+
+
+def _setup_both(G, O, **kw):
+    G.setup(krylov=1, **kw)
+    O.setup(krylov=1, **{k: v for k, v in kw.items() if k in ("mode", "smoother", "level_smoother", "tol",
+                                                                 "max_iter", "restart")})
+
+
+def _compare(st, ref, x, hist_tol=RTOL_ITER):
+    assert ref["status"] == 0 and st["status"][0] == 0
+    assert abs(st["iters"][0] - ref["iters"]) <= 1, (st["iters"][0], ref["iters"])
+    h = st["hist"][:, 0]
+    m = min(len(h), len(ref["hist"]))
+    dev = np.abs(h[:m] - ref["hist"][:m]) / ref["hist"][0]
+    assert dev.max() <= hist_tol, dev.max()
+    assert st["true_rel"][0] <= 1e-8
+    xo = ref["x"]
+    assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("graph", [1, 0])
+def test_fgmres_history(pair, torch_cuda, mode, graph):
+    _, G, O = pair
+    _setup_both(G, O, mode=mode, restart=30, use_graph=graph)
+    ref = O.solve()
+    x, st = G.solve(G.rhs(), hist_cap=600)
+    _compare(st, ref, x.cpu().numpy())
+
+
+@pytest.mark.parametrize("m", [1, 4])
+def test_fgmres_with_restarts(pair, torch_cuda, m):
+    """Short cycles: the true residual restarts every m steps (m = 1 is a minimal
+    residual step per cycle)."""
+    torch = torch_cuda
+    _, G, O = pair
+    _setup_both(G, O, restart=m, max_iter=2000)
+    b = rhs_normal(G.nh, 1, 3)[:, 0]
+    ref = O.solve(b)
+    x, st = G.solve(torch.tensor(b, device="cuda"), hist_cap=2500)
+    _compare(st, ref, x.cpu().numpy())
+    assert st["restarts"] >= (ref["iters"] - 1) // m
+
+
+def test_fgmres_graph_equals_eager_bitwise(pair, torch_cuda):
+    torch = torch_cuda
+    _, G, O = pair
+    b = G.rhs()
+    outs = []
+    for graph in (1, 1, 0):
+        G.setup(krylov=1, restart=8, use_graph=graph, spmv_threads=4)
+        x, st = G.solve(b, hist_cap=600)
+        outs.append((x.cpu().numpy(), st["hist"][:, 0]))
+    for x, h in outs[1:]:
+        assert np.array_equal(x, outs[0][0]) and np.array_equal(h, outs[0][1])
+
+
+def test_fgmres_fp32_preconditioner(pair, torch_cuda):
+    """FP32 preconditioner inside FGMRES (flexible by construction): reaches 1e-8; the
+    solution's error against the FP64 oracle is stated by the bound."""
+    _, G, O = pair
+    G.setup(krylov=1, precond_precision=1)
+    O.setup(krylov=1)
+    ref = O.solve()
+    x, st = G.solve(G.rhs())
+    assert st["status"][0] == 0 and st["true_rel"][0] <= 1e-8
+    assert abs(st["iters"][0] - ref["iters"]) <= 3
+    err = np.linalg.norm(x.cpu().numpy() - ref["x"]) / np.linalg.norm(ref["x"])
+    assert err <= 1e-6, err
+
+
+def test_fgmres_limits_and_degenerate_inputs(pair, torch_cuda):
+    torch = torch_cuda
+    _, G, O = pair
+    from paper_1204_2586_gb300 import PkaspError
+    from paper_1204_2586_gb300 import _lib as L
+
+    G.setup(krylov=1, max_iter=3)
+    _, st = G.solve(G.rhs(), raise_on_fail=False)
+    assert st["rc"] == L.PKASP_ENOTCONV and st["iters"][0] == 3
+    G.setup(krylov=1)
+    z = torch.zeros(G.nh, dtype=torch.float64, device="cuda")
+    x, st = G.solve(z)
+    assert st["status"][0] == 0 and st["iters"][0] == 0 and torch.count_nonzero(x).item() == 0
+    with pytest.raises(PkaspError) as e:
+        G.solve(torch.zeros(G.nh, 2, dtype=torch.float64, device="cuda"))
+    assert e.value.code == L.PKASP_EINVAL
+    with pytest.raises(PkaspError) as e:
+        G.setup(krylov=1, restart=0)
+    assert e.value.code == L.PKASP_EINVAL
+    G.setup()
