@@ -134,13 +134,22 @@ __global__ void __launch_bounds__(kBlock) kg_dots(int64_t n, const double *__res
     }
     __syncthreads();
     if (!last) return;
+    // the chunk partials, summed by the whole block in a fixed tree (thread t adds chunks
+    // t, t + blockDim, ... in order; then warps, then the warp sums in order)
+    __threadfence();
+    double t = 0.0;
+    for (unsigned c = threadIdx.x; c < gridDim.x; c += blockDim.x) t += __ldcg(&part[(int64_t)i * gridDim.x + c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        double t = 0.0;
-        for (unsigned c = 0; c < gridDim.x; ++c) t += __ldcg(&part[(int64_t)i * gridDim.x + c]);
-        hc[i] = t;
-        if (pass == 0) H[i * m + j] = t;
-        else H[i * m + j] += t;
+        double u = 0.0;
+        for (int k = 0; k < kBlock / 32; ++k) u += sh[k];
+        hc[i] = u;
+        if (pass == 0) H[i * m + j] = u;
+        else H[i * m + j] += u;
         cnt[i] = 0u;
     }
 }
@@ -154,6 +163,7 @@ __global__ void __launch_bounds__(kBlock) kg_axpy(int64_t n, const double *__res
     double part = 0.0;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         double x = w[q];
+#pragma unroll 4
         for (int i = 0; i <= j; ++i) x -= hc[i] * V[(int64_t)i * n + q];
         w[q] = x;
         part += x * x;

@@ -40,22 +40,22 @@ constexpr int kBatch = 8;
 
 // sum_{e in [lo,hi)} val[e] * x[col[e]] accumulated in A by the lanes of a sub-warp,
 // lane `sub` adding entries lo+sub, lo+sub+TPR, ... in that order
-template <int TPR, typename A, typename VT, typename XT>
+template <int TPR, typename A, typename VT, typename XT, int NB = kBatch>
 __device__ __forceinline__ A row_dot(int64_t lo, int64_t hi, int sub, const int32_t *__restrict__ col,
                                      const VT *__restrict__ val, const XT *__restrict__ x) {
     A acc = A(0);
-    for (int64_t base = lo + sub; base < hi; base += kBatch * TPR) {
-        int c[kBatch];
-        A v[kBatch];
+    for (int64_t base = lo + sub; base < hi; base += NB * TPR) {
+        int c[NB];
+        A v[NB];
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
+        for (int k = 0; k < NB; ++k) {
             const int64_t e = base + (int64_t)k * TPR;
             const bool ok = e < hi;
             c[k] = ok ? ldg(&col[e]) : -1;
             v[k] = ok ? (A)ldg(&val[e]) : A(0);
         }
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k)
+        for (int k = 0; k < NB; ++k)
             if (c[k] >= 0) acc += v[k] * (A)ldg(&x[c[k]]);
     }
     return subwarp_sum<TPR>(acc);
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kBlock) k_gs_bwd0(int64_t pb, int64_t pe, cons
     if (lead) y[i] = yi - s / d;
 }
 
-template <int TPR, typename PT>
+template <int TPR, int NB, typename PT>
 __global__ void __launch_bounds__(kBlock) k_gs_bwd_full(int64_t pb, int64_t pe, const int32_t *__restrict__ perm,
                                                         const int64_t *__restrict__ lptr, const int32_t *__restrict__ lcol,
                                                         const PT *__restrict__ lval, const int64_t *__restrict__ uptr,
@@ -344,8 +344,8 @@ __global__ void __launch_bounds__(kBlock) k_gs_bwd_full(int64_t pb, int64_t pe, 
     const int64_t llo = ok ? lptr[p] : 0, lhi = ok ? lptr[p + 1] : 0;
     const int64_t ulo = ok ? uptr[p] : 0, uhi = ok ? uptr[p + 1] : 0;
     const PT bi = lead ? b[i] : PT(0);
-    PT sl = row_dot<TPR, PT>(llo, lhi, sub, lcol, lval, (const PT *)x);
-    PT su = row_dot<TPR, PT>(ulo, uhi, sub, ucol, uval, (const PT *)x);
+    PT sl = row_dot<TPR, PT, PT, PT, NB>(llo, lhi, sub, lcol, lval, (const PT *)x);
+    PT su = row_dot<TPR, PT, PT, PT, NB>(ulo, uhi, sub, ucol, uval, (const PT *)x);
     if (lead) x[i] = (bi - sl - su) / d;
 }
 

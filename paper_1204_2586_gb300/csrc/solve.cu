@@ -192,9 +192,10 @@ void gs_backward_full(const DSplit &sp, int tpr_fixed, const PT *b, PT *x, cudaS
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
         const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(std::max(sp.lmax[c], sp.umax[c]));
-        PK_TPR_SWITCH(tpr, (k_gs_bwd_full<TPR, PT><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
+        const int nb = batch_for(tpr, std::max(sp.l90[c], sp.u90[c]));
+        PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (k_gs_bwd_full<TPR, NB, PT><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
                                 pb, pe, sp.perm, sp.lptr, sp.lcol, pick<PT>(sp.lval, sp.lval32), sp.uptr,
-                                sp.ucol, pick<PT>(sp.uval, sp.uval32), pick<PT>(sp.diag, sp.diag32), b, x)));
+                                sp.ucol, pick<PT>(sp.uval, sp.uval32), pick<PT>(sp.diag, sp.diag32), b, x))));
         PK_LAUNCH();
     }
 }
@@ -377,7 +378,9 @@ void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s) 
     const bool jac = p->opt.smoother == PKASP_SMOOTHER_L1JACOBI;
     // the full backward sweep uses the CSR split (one row per lane group)
     const int ts = p->fine_tpr > 100 ? p->fine_tpr - 100 : p->fine_tpr > 0 ? p->fine_tpr : -1;
-    const int ta = p->spmv_tpr;
+    // the residuals read the CSR form (a SELL-32 choice of the autotuner maps to the
+    // lanes fitted to the mean row length)
+    const int ta = p->spmv_tpr > 0 ? p->spmv_tpr : tpr_of(p->Ah);
     PT *t = pickw<PT>(p->w_t, p->w_t32);
     PT *rr = pickw<PT>(p->w_rr, p->w_rr32);
     if (jac) {
