@@ -80,9 +80,10 @@ typedef struct {
                              32; 0 = pick by mean row length [0] */
     int smoother_layout;  /* fine smoother layout (SGS): 0 = autotuned at setup [0];
                              1 = one launch per colour phase, CSR, lanes fitted per colour;
-                             2 = per phase, SELL-32; 4, 8, 16 = per phase, CSR with that
-                             many lanes per row; 104, 108, 116 = per phase, CSR with 4, 8,
-                             16 lanes and two rows per lane group; -4, -8, -16 = the whole
+                             2 = per phase, SELL-32; 3 = per phase, CSR with 2 lanes per
+                             row; 4, 8, 16 = per phase, CSR with that many lanes per row;
+                             102, 104, 108, 116 = per phase, CSR with 2, 4, 8, 16 lanes and
+                             two rows per lane group; -4, -8, -16 = the whole
                              symmetric sweep in one cooperative launch with that many
                              lanes per row.
                              spmv_threads != 0 overrides it with its own lane count. */

@@ -119,15 +119,16 @@ int lanes_for(int len) {
 // (90th percentile) have at most `len` entries: the fewest of 2, 4, 8 that cover such a
 // row in one batch (else 8); longer rows take further batches.
 int batch_for(int tpr, int len) {
-    for (int nb : {2, 4})
+    for (int nb : {2, 4, 8})
         if (nb * tpr >= len) return nb;
-    return 8;
+    return tpr <= 2 ? 16 : 8;  // two lanes per row: up to 32 entries in one batch
 }
 
 #define PK_NB_SWITCH(nb, BODY)                           \
     switch (nb) {                                        \
         case 2: { constexpr int NB = 2; BODY; } break;   \
         case 4: { constexpr int NB = 4; BODY; } break;   \
+        case 16: { constexpr int NB = 16; BODY; } break; \
         default: { constexpr int NB = 8; BODY; } break;  \
     }
 
@@ -635,8 +636,8 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
     }
     // a fixed smoother layout: internal code -1 per-colour lanes, 0 SELL-32, t lanes
     // 100 + t (t lanes, two rows per sub-warp) passes through
-    const int fixed_fine = p->opt.smoother_layout == 1 ? -1 : p->opt.smoother_layout == 2 ? 0
-                                                                                           : p->opt.smoother_layout;
+    const int lay = p->opt.smoother_layout;
+    const int fixed_fine = lay == 1 ? -1 : lay == 2 ? 0 : lay == 3 ? 2 : lay;
     cudaEvent_t e0, e1;
     PK_CUDA(cudaEventCreate(&e0));
     PK_CUDA(cudaEventCreate(&e1));
@@ -674,6 +675,8 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
     // 100 + t: t lanes, two rows per sub-warp. The one-launch cooperative sweep (-t) is
     // not a candidate: its grid barrier cost more than a phase launch on every measured
     // problem (P3 32^3, P4 48^3); smoother_layout selects it explicitly.
+    // (2 lanes per row, layouts 3 and 102, lost on every measured problem: P3 32^3 FP64
+    // 769 vs 467 us; they stay selectable through smoother_layout)
     const int cand_fine[] = {-1, 0, 4, 8, 16, 104, 108, 116};
     const int pick_spmv = tune(cand_spmv, 4, &p->spmv_tpr, [&] { spmv_fine(p, p->d_b, p->w_q, s); });
     p->spmv_tpr = pick_spmv;
