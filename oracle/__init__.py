@@ -382,8 +382,14 @@ class Problem:
         return z
 
     def vcycle(self, b):
-        x = np.zeros(self.nH)
-        lib().orc_vcycle(self.h, _f64(b), x)
+        """One V-cycle on level 0 of the hierarchy (A_H, or A_h in plain AMG mode)."""
+        info = np.zeros(4, np.int64)
+        lib().orc_level_info(self.h, 0, info)
+        b = _f64(b)
+        if b.shape[0] != int(info[0]):
+            raise ValueError("vcycle input must have the size of level 0")
+        x = np.zeros(int(info[0]))
+        lib().orc_vcycle(self.h, b, x)
         return x
 
     def solve(self, b=None, x0=None, hist_cap=1024):

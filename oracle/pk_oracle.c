@@ -1452,7 +1452,9 @@ int orc_setup(oproblem *P, const oopts *o) {
                                  P->colour_h);
     P->l1_h = l1_norms(P->Ah);
     int maxl = o->max_levels < 1 ? 1 : (o->max_levels > MAXLEV ? MAXLEV : o->max_levels);
-    ocsr *A = P->AH;
+    /* mode 2: plain AMG, the hierarchy starts from A_h itself (the comparison method of
+       Sec. 1 and Sec. 6.2); otherwise from the P1 matrix A_H of the auxiliary space */
+    ocsr *A = o->mode == 2 ? P->Ah : P->AH;
     int l = 0;
     for (;;) {
         olevel *L = &P->lev[l];
@@ -1563,7 +1565,10 @@ void orc_apply_prec(oproblem *P, const double *r, double *z) {
     double *rH = (double *)xmalloc(sizeof(double) * (size_t)(nH ? nH : 1));
     double *wH = (double *)xmalloc(sizeof(double) * (size_t)(nH ? nH : 1));
     double *t = (double *)xmalloc(sizeof(double) * (size_t)(nh ? nh : 1));
-    if (P->o.mode == 0) {
+    if (P->o.mode == 2) {
+        /* plain AMG: one V-cycle on the hierarchy of A_h */
+        orc_vcycle(P, r, z);
+    } else if (P->o.mode == 0) {
         orc_smoother(P, r, z);
         orc_spmv(P->PiT, r, rH);
         orc_vcycle(P, rH, wH);

@@ -16,7 +16,8 @@ typedef struct oproblem oproblem;
 
 typedef struct {
     double theta;        /* strength threshold (Sec. 6.2), default 0.25 */
-    int mode;            /* 0 additive B = S + Pi V Pi^T, 1 multiplicative (Alg. 2.1 + Remark 2.1) */
+    int mode;            /* 0 additive B = S + Pi V Pi^T, 1 multiplicative (Alg. 2.1 + Remark 2.1),
+                            2 plain AMG: one V-cycle of the AMG hierarchy of A_h itself */
     int smoother;        /* P_k smoother: 0 multicolour symmetric GS, 1 l1-Jacobi */
     int level_smoother;  /* AMG level smoother: 0 multicolour GS, 1 l1-Jacobi */
     int coarse_size;     /* stop coarsening at or below this many rows */

@@ -434,7 +434,51 @@ def test_two_level_closed_form(oracle_mod, mode):
     assert np.linalg.eigvalsh(0.5 * (Bm + Bm.T)).min() > 0
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("lsm", [0, 1])
+def test_plain_amg_two_level_closed_form(oracle_mod, lsm):
+    """Plain AMG on A_h (the comparison method), two levels with the exact coarse solve:
+    one V(1,1)-cycle has error operator (I - S_b A)(I - P A_c^{-1} P^T A)(I - S_f A)
+    with A_c = P^T A P, S_f / S_b the forward / backward multicolour GS of level 0 in its
+    colour order (lsm = 0) or the l1-Jacobi step D_l1^{-1} (lsm = 1)."""
+    xyz, t = _mesh(3)
+    P = oracle_mod.Problem(xyz, t, 2, kappa_lognormal(t.shape[0], 1))
+    P.setup(mode=2, level_smoother=lsm, max_levels=2, coarse_size=1)
+    assert P.levels() == 2
+    A = P.matrix(0).to_scipy().toarray()
+    L0 = P.level(0)
+    assert np.array_equal(L0["A"].ptr, P.matrix(0).ptr)  # level 0 is A_h itself
+    Pm = L0["P"].to_scipy().toarray()
+    n = A.shape[0]
+    I = np.eye(n)
+    if lsm == 0:
+        c = L0["colour"]
+        perm = np.lexsort((np.arange(n), c))
+        inv = np.argsort(perm)
+        Ap = A[np.ix_(perm, perm)]
+        D = np.diag(np.diag(Ap))
+        Sf = np.linalg.inv(D + np.tril(Ap, -1))[np.ix_(inv, inv)]
+        Sb = np.linalg.inv(D + np.triu(Ap, 1))[np.ix_(inv, inv)]
+    else:
+        Sf = Sb = np.diag(1.0 / np.abs(A).sum(axis=1))
+    Ac = Pm.T @ A @ Pm
+    E = (I - Sb @ A) @ (I - Pm @ np.linalg.solve(Ac, Pm.T @ A)) @ (I - Sf @ A)
+    Bm = np.column_stack([P.apply_prec(I[:, j]) for j in range(n)])
+    assert np.abs((I - Bm @ A) - E).max() <= 1e-10
+
+
+def test_plain_amg_pcg_reaches_dense_solution(oracle_mod):
+    xyz, t = _mesh(3)
+    P = oracle_mod.Problem(xyz, t, 3, kappa_lognormal(t.shape[0], 1))
+    P.setup(mode=2, coarse_size=20, tol=1e-12)
+    assert P.levels() >= 3
+    out = P.solve()
+    assert out["status"] == 0
+    A = P.matrix(0).to_scipy().toarray()
+    u = np.linalg.solve(A, P.rhs())
+    assert np.linalg.norm(out["x"] - u) <= 1e-9 * np.linalg.norm(u)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("lsm", [0, 1])
 def test_multilevel_preconditioner_symmetric_positive(oracle_mod, mode, lsm):
     xyz, t = _mesh(5)
@@ -446,8 +490,9 @@ def test_multilevel_preconditioner_symmetric_positive(oracle_mod, mode, lsm):
     bx, by = P.apply_prec(x), P.apply_prec(y)
     assert abs(y @ bx - x @ by) <= 1e-12 * abs(y @ bx)
     assert x @ bx > 0
-    # the V-cycle on its own is symmetric too
-    u, v = rng.standard_normal(P.nH), rng.standard_normal(P.nH)
+    # the V-cycle on its own is symmetric too (level 0: A_H, or A_h in plain AMG mode)
+    n0 = P.nh if mode == 2 else P.nH
+    u, v = rng.standard_normal(n0), rng.standard_normal(n0)
     assert abs(v @ P.vcycle(u) - u @ P.vcycle(v)) <= 1e-12 * abs(v @ P.vcycle(u))
 
 
