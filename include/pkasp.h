@@ -49,7 +49,7 @@ enum {
     PKASP_ESTATE = 7      /* call out of order (e.g. solve before setup) */
 };
 
-enum { PKASP_MODE_ADDITIVE = 0, PKASP_MODE_MULTIPLICATIVE = 1 };
+enum { PKASP_MODE_ADDITIVE = 0, PKASP_MODE_MULTIPLICATIVE = 1, PKASP_MODE_AMG = 2 };
 enum { PKASP_SMOOTHER_SGS = 0, PKASP_SMOOTHER_L1JACOBI = 1 };
 enum { PKASP_PREC_FP64 = 0, PKASP_PREC_FP32 = 1 };
 enum { PKASP_KRYLOV_CG = 0, PKASP_KRYLOV_FGMRES = 1 };
@@ -60,7 +60,9 @@ enum { PKASP_MAX_LEVELS = 25, PKASP_MAX_COLS = 64 };
 typedef struct {
     double theta;         /* strength threshold of Sec. 6.2 [0.25] */
     int mode;             /* PKASP_MODE_*: additive z = S_k r + Pi V(Pi^T r) [additive];
-                             multiplicative = Algorithm 2.1 with pre-smoothing (Remark 2.1) */
+                             multiplicative = Algorithm 2.1 with pre-smoothing (Remark 2.1);
+                             AMG = one V-cycle of an AMG hierarchy built on A_h itself, the
+                             comparison method of the paper (Sec. 1, Table 1, Sec. 6.2) */
     int smoother;         /* P_k smoother S_k: PKASP_SMOOTHER_* [SGS: one forward and one
                              backward multicolour Gauss-Seidel sweep, Remark 6.1] */
     int level_smoother;   /* AMG level smoother, PKASP_SMOOTHER_* [SGS] */

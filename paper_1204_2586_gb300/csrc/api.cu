@@ -233,7 +233,7 @@ int pkasp_setup(pkasp_problem *p, const pkasp_options *opt, pkasp_stream_t strea
     if (opt) o = *opt;
     else pkasp_default_options(&o);
     if (!(o.theta >= 0.0 && o.theta < 1.0)) return set_error(PKASP_EINVAL, "theta must be in [0, 1)");
-    if (o.mode != 0 && o.mode != 1) return set_error(PKASP_EINVAL, "unknown mode");
+    if (o.mode != 0 && o.mode != 1 && o.mode != 2) return set_error(PKASP_EINVAL, "unknown mode");
     if (o.smoother != 0 && o.smoother != 1) return set_error(PKASP_EINVAL, "unknown smoother");
     if (o.level_smoother != 0 && o.level_smoother != 1) return set_error(PKASP_EINVAL, "unknown level smoother");
     if (o.max_levels < 1 || o.max_levels > PKASP_MAX_LEVELS) return set_error(PKASP_EINVAL, "max_levels out of range");

@@ -835,6 +835,17 @@ struct Batched {
     // its two branches on two streams
     template <typename PT>
     static void precondition(pkasp_problem *p, const PT *R, double *Z, cudaStream_t s) {
+        if (p->opt.mode == PKASP_MODE_AMG) {
+            // plain AMG: one V-cycle on the hierarchy of A_h (level 0 is A_h)
+            const int64_t ne = p->nh * NC;
+            const unsigned eg = (unsigned)((ne + kBlock - 1) / kBlock);
+            kb_copy<PT, PT><<<eg, kBlock, 0, s>>>(ne, R, bpickw<PT>(p->bl_b[0], p->bl_b32[0]));
+            PK_LAUNCH();
+            vcycle<PT>(p, 0, s);
+            kb_copy<double, PT><<<eg, kBlock, 0, s>>>(ne, bpickw<PT>(p->bl_x[0], p->bl_x32[0]), Z);
+            PK_LAUNCH();
+            return;
+        }
         if (p->opt.mode != PKASP_MODE_ADDITIVE) return multiplicative<PT>(p, R, Z, s);
         PT *zs = bpickw<PT>(p->bw_zs, p->bw_zs32);
         PK_CUDA(cudaEventRecord(p->ev_fork, s));

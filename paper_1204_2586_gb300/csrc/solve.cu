@@ -361,6 +361,14 @@ template <typename PT>
 void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s) {
     PT *zs = pickw<PT>(p->w_zs, p->w_zs32);
     Level &L0 = p->lev[0];
+    if (p->opt.mode == PKASP_MODE_AMG) {
+        // plain AMG: one V-cycle on the hierarchy of A_h (level 0 is A_h)
+        to_pt<PT>(r, lv_b<PT>(L0), p->nh, s);
+        vcycle<PT>(p, 0, s);
+        k_copy_to<PT><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, lv_x<PT>(L0), z);
+        PK_LAUNCH();
+        return;
+    }
     if (p->opt.mode == PKASP_MODE_ADDITIVE) {
         // fork: the V-cycle branch runs on the auxiliary stream, the smoother on s
         PK_CUDA(cudaEventRecord(p->ev_fork, s));
@@ -722,7 +730,10 @@ void setup_device(pkasp_problem *p, cudaStream_t s) {
     p->lev.clear();
     p->lev.reserve(maxl);
     p->lev.emplace_back();
-    p->lev[0].A = p->AH;  // level 0 aliases the assembled A_H (owned by the problem)
+    // level 0 aliases an assembled operator owned by the problem: A_H of the auxiliary
+    // space, or A_h itself for plain AMG
+    const bool amg = o.mode == PKASP_MODE_AMG;
+    p->lev[0].A = amg ? p->Ah : p->AH;
     for (int l = 0;; ++l) {
         Level &L = p->lev[l];
         build_split(pool, L.A, stream_colour(o.seed, 1 + l), want32, L.sp, s);
@@ -748,7 +759,7 @@ void setup_device(pkasp_problem *p, cudaStream_t s) {
             L.x32 = pool.get<float>(n);
             L.r32 = pool.get<float>(n);
             if (l > 0) dcsr_make32(pool, L.A, s);
-            else L.A.val32 = p->AH.val32;
+            else L.A.val32 = amg ? p->Ah.val32 : p->AH.val32;
             L.l132 = pool.get<float>(n);
             to32(L.l1, L.l132, L.A.n, s);
             if (L.P.n) {

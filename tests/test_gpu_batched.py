@@ -59,7 +59,7 @@ def _check_column(st, c, ref, x, hist_tol=RTOL_ITER):
     assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("mode,graph", [(0, 1), (0, 0), (1, 1)])
+@pytest.mark.parametrize("mode,graph", [(0, 1), (0, 0), (1, 1), (2, 1)])
 def test_columns_match_oracle(pair, torch_cuda, mode, graph):
     torch = torch_cuda
     _, G, O = pair

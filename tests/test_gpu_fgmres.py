@@ -56,7 +56,7 @@ def _compare(st, ref, x, hist_tol=RTOL_ITER):
     assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("graph", [1, 0])
 def test_fgmres_history(pair, torch_cuda, mode, graph):
     _, G, O = pair

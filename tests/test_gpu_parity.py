@@ -89,10 +89,14 @@ def _setup_both(G, O, **kw):
     O.setup(**okw)
 
 
-def test_colourings_and_hierarchy(pair):
-    """Colourings, strength flags and C/F splittings are integer decisions: bit-exact."""
+@pytest.mark.parametrize("mode", [0, 2])
+def test_colourings_and_hierarchy(pair, mode):
+    """Colourings, strength flags and C/F splittings are integer decisions: bit-exact.
+    mode 2 (plain AMG) builds the hierarchy on A_h itself."""
     _, G, O = pair
-    _setup_both(G, O)
+    _setup_both(G, O, mode=mode)
+    if mode == 2:
+        assert G.info.level_rows[0] == G.nh
     gc, gn = G.colours(-1)
     assert np.array_equal(gc, O.fine_colour()) and gn == gc.max() + 1
     assert G.info.levels == O.levels()
@@ -127,7 +131,7 @@ def test_pmis_bit_exact_on_oracle_strength(pair, torch_cuda):
         assert np.array_equal(cf_g, cf_o)
 
 
-@pytest.mark.parametrize("mode,sm,lsm", [(0, 0, 0), (0, 1, 1), (1, 0, 0), (1, 1, 0)])
+@pytest.mark.parametrize("mode,sm,lsm", [(0, 0, 0), (0, 1, 1), (1, 0, 0), (1, 1, 0), (2, 0, 0), (2, 0, 1)])
 def test_preconditioner_pieces(pair, torch_cuda, mode, sm, lsm):
     torch = torch_cuda
     _, G, O = pair
@@ -136,12 +140,12 @@ def test_preconditioner_pieces(pair, torch_cuda, mode, sm, lsm):
     r = rng.standard_normal(G.nh)
     rt = torch.tensor(r, device="cuda")
     _rel_close(G.apply_smoother(rt).cpu().numpy(), O.smoother(r), RTOL_OP)
-    bH = rng.standard_normal(G.nH)
+    bH = rng.standard_normal(G.nh if mode == 2 else G.nH)
     _rel_close(G.apply_vcycle(torch.tensor(bH, device="cuda")).cpu().numpy(), O.vcycle(bH), 1e-11)
     _rel_close(G.apply_prec(rt).cpu().numpy(), O.apply_prec(r), 1e-11)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("graph", [1, 0])
 def test_pcg_history(pair, torch_cuda, mode, graph):
     """Per-iteration residual norms match the oracle's to 1e-10 relative to ||r_0||
