@@ -220,7 +220,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD["name"], choices=[WORKLOAD["name"], P4["name"], BATCHED["name"]])
+    ap.add_argument("--workload", default=WORKLOAD["name"],
+                    choices=[WORKLOAD["name"], P4["name"], BATCHED["name"], "theta_study"])
     ap.add_argument("--smoother-layout", type=int, default=0,
                     help="pin the fine smoother layout (pkasp_options.smoother_layout) instead of "
                          "autotuning it; for profiler runs, under which the autotuner's timings "
@@ -253,6 +254,9 @@ def main():
     from paper_1204_2586_gb300 import build
 
     build.build()
+    if args.workload == "theta_study":
+        run_theta_study(args)
+        return
     if args.workload == BATCHED["name"]:
         run_batched(args, ws, rank, local)
         if ws > 1:
@@ -420,6 +424,43 @@ def main():
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+THETA_STUDY = [(2, 32), (3, 24), (4, 16)]  # (k, cubes per side)
+
+
+def run_theta_study(args):
+    """Iteration counts and times of the auxiliary-space preconditioner (additive PCG)
+    against plain AMG on A_h (one V-cycle, PCG), for strength thresholds 0.25 / 0.5 / 0.8:
+    the comparison of the paper's Table 1 (AMG on P_k matrices degrades as theta and k
+    grow) and Tables 2-4 (the auxiliary space is robust in theta). Prints one JSON line."""
+    import torch
+
+    from paper_1204_2586_gb300 import Problem
+    from paper_1204_2586_gb300.inputs import kuhn_mesh
+
+    rows = []
+    for k, n in THETA_STUDY:
+        xyz, t = kuhn_mesh(n, 0.2, 0)
+        G = Problem(xyz, t, k)
+        b = G.rhs()
+        for theta in (0.25, 0.5, 0.8):
+            for mode, name in ((0, "aux_space_additive"), (2, "plain_amg")):
+                t0 = time.perf_counter()
+                G.setup(theta=theta, mode=mode, level_smoother=LEVEL_SMOOTHER, max_iter=2000)
+                torch.cuda.synchronize()
+                setup_s = time.perf_counter() - t0
+                x = torch.zeros_like(b)
+                G.solve(b, x, raise_on_fail=False)
+                x.zero_()
+                _, st = G.solve(b, x, raise_on_fail=False)
+                info = G.info
+                rows.append({"k": k, "n": n, "n_h": G.nh, "theta": theta, "method": name,
+                             "iterations": st["iters"][0], "status": st["status"][0],
+                             "solve_s": st["solve_ms"] / 1e3, "setup_s": setup_s,
+                             "levels": int(info.levels), "op_complexity": info.op_complexity})
+        G.close()
+    print(json.dumps({"study": "theta", "tol": 1e-8, "krylov": "PCG", "rows": rows}))
 
 
 def run_batched(args, ws, rank, local):

@@ -110,7 +110,8 @@ typedef struct {
     int64_t level_rows[PKASP_MAX_LEVELS];
     int64_t level_nnz[PKASP_MAX_LEVELS];
     int level_colours[PKASP_MAX_LEVELS];
-    double op_complexity;   /* sum_l nnz(A_l) / nnz(A_H) (Sec. 6.2, Table 6) */
+    double op_complexity;   /* sum_l nnz(A_l) / nnz(A_0), A_0 = A_H (A_h in plain AMG
+                               mode) (Sec. 6.2, Table 6) */
     double setup_ms, assemble_ms;
     int spmv_layout;        /* autotuned layout of the fine SpMV: 0 = SELL-32 (one thread
                                per row), t > 0 = CSR read by t lanes per row */

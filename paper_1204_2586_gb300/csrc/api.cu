@@ -188,7 +188,9 @@ int pkasp_problem_info(const pkasp_problem *p, pkasp_info *info) {
             info->level_colours[l] = p->lev[l].sp.ncol;
             tot += (double)p->lev[l].A.nnz;
         }
-        info->op_complexity = p->AH.nnz > 0 ? tot / (double)p->AH.nnz : 0;
+        // relative to level 0: A_H, or A_h in plain AMG mode
+        const int64_t nnz0 = p->lev.empty() ? 0 : p->lev[0].A.nnz;
+        info->op_complexity = nnz0 > 0 ? tot / (double)nnz0 : 0;
         info->setup_ms = p->setup_ms;
         info->spmv_layout = p->spmv_tpr;
         info->smoother_layout = p->fine_tpr;
