@@ -40,7 +40,7 @@ class OOpts(C.Structure):
                 ("level_smoother", C.c_int), ("coarse_size", C.c_int),
                 ("max_levels", C.c_int), ("seed", C.c_uint64), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("flexible", C.c_int), ("krylov", C.c_int),
-                ("restart", C.c_int)]
+                ("restart", C.c_int), ("interp_pmax", C.c_int), ("interp_trunc", C.c_int)]
 
 
 def lib():
@@ -78,6 +78,8 @@ def lib():
     L.orc_pmis.argtypes = [vp, u8p, C.c_uint64, i8p]
     L.orc_extpi.restype = vp
     L.orc_extpi.argtypes = [vp, u8p, i8p]
+    L.orc_truncate.restype = vp
+    L.orc_truncate.argtypes = [vp, C.c_double, C.c_int]
     L.orc_transpose.restype = vp
     L.orc_transpose.argtypes = [vp]
     L.orc_spgemm.restype = vp
@@ -220,6 +222,15 @@ def colour_jp(a: CSR, stream: int):
     return c, int(nc)
 
 
+def truncate(p: CSR, tf: float, pmax: int) -> CSR:
+    """Interpolation truncation (drop small weights, keep the largest, keep row sums)."""
+    h = p.handle()
+    try:
+        return _take(lib().orc_truncate(h, float(tf), int(pmax)))
+    finally:
+        free_csr(h)
+
+
 def strength(a: CSR, theta: float):
     h = a.handle()
     s = np.zeros(max(a.nnz, 1), np.uint8)
@@ -279,7 +290,8 @@ SOURCE_NONE, SOURCE_SINE = 0, 1
 
 def default_opts(**kw) -> OOpts:
     o = OOpts(theta=0.25, mode=0, smoother=0, level_smoother=0, coarse_size=256,
-              max_levels=25, seed=0, tol=1e-8, max_iter=500, flexible=0, krylov=0, restart=30)
+              max_levels=25, seed=0, tol=1e-8, max_iter=500, flexible=0, krylov=0, restart=30,
+              interp_pmax=0, interp_trunc=0)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

@@ -1444,6 +1444,81 @@ static void chol_solve(const double *L, int64_t n, const double *b, double *x) {
  *     solved approximately by one AMG cycle, Remark 2.1). Coarsening stops at
  *     coarse_size rows, at max_levels, or when PMIS keeps no or all points.
  * ---------------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------------------
+ * Interpolation truncation (optional; the paper's BoomerAMG settings are not stated):
+ * in every row of P, drop the weights with |w| < tf * max|w|, then keep the pmax
+ * largest |w| (ties: the lower column first), then scale the kept weights so that the
+ * row sum equals the row sum before truncation. tf = 0 and pmax = 0 leave P as it is.
+ * Rows of coarse points (one weight 1) are unchanged by construction.
+ * ---------------------------------------------------------------------------------- */
+ocsr *orc_truncate(const ocsr *p, double tf, int pmax) {
+    const int64_t n = p->nrows;
+    int64_t *pp = (int64_t *)xcalloc((size_t)n + 1, sizeof(int64_t));
+    int32_t *pc = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(p->nnz ? p->nnz : 1));
+    double *pv = (double *)xmalloc(sizeof(double) * (size_t)(p->nnz ? p->nnz : 1));
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t lo = p->ptr[i], hi = p->ptr[i + 1];
+        double mx = 0.0, sum = 0.0;
+        for (int64_t e = lo; e < hi; ++e) {
+            mx = fmax(mx, fabs(p->val[e]));
+            sum += p->val[e];
+        }
+        const int64_t start = nnz;
+        for (int64_t e = lo; e < hi; ++e) {
+            if (tf > 0.0 && fabs(p->val[e]) < tf * mx) continue;
+            pc[nnz] = p->col[e];
+            pv[nnz] = p->val[e];
+            ++nnz;
+        }
+        if (pmax > 0 && nnz - start > pmax) {
+            /* keep the pmax largest |w|: repeated selection, ties to the lower column */
+            int64_t cnt = nnz - start;
+            int32_t *kc = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)cnt);
+            double *kv = (double *)xmalloc(sizeof(double) * (size_t)cnt);
+            char *taken = (char *)xcalloc((size_t)cnt, 1);
+            for (int q = 0; q < pmax; ++q) {
+                int64_t best = -1;
+                for (int64_t e = 0; e < cnt; ++e) {
+                    if (taken[e]) continue;
+                    const double a = fabs(pv[start + e]);
+                    if (best < 0 || a > fabs(pv[start + best]) ||
+                        (a == fabs(pv[start + best]) && pc[start + e] < pc[start + best]))
+                        best = e;
+                }
+                taken[best] = 1;
+            }
+            int64_t m = 0;
+            for (int64_t e = 0; e < cnt; ++e)
+                if (taken[e]) {
+                    kc[m] = pc[start + e];
+                    kv[m] = pv[start + e];
+                    ++m;
+                }
+            for (int64_t e = 0; e < m; ++e) {
+                pc[start + e] = kc[e];
+                pv[start + e] = kv[e];
+            }
+            nnz = start + m;
+            free(kc);
+            free(kv);
+            free(taken);
+        }
+        double kept = 0.0;
+        for (int64_t e = start; e < nnz; ++e) kept += pv[e];
+        if (nnz - start < hi - lo && kept != 0.0) {
+            const double scale = sum / kept;
+            for (int64_t e = start; e < nnz; ++e) pv[e] *= scale;
+        }
+        pp[i + 1] = nnz;
+    }
+    ocsr *t = orc_csr_new(n, p->ncols, nnz, pp, pc, pv);
+    free(pp);
+    free(pc);
+    free(pv);
+    return t;
+}
+
 int orc_setup(oproblem *P, const oopts *o) {
     free_levels(P);
     P->o = *o;
@@ -1473,6 +1548,11 @@ int orc_setup(oproblem *P, const oopts *o) {
         for (int64_t i = 0; i < A->nrows; ++i) nc += (L->cf[i] == 1);
         if (nc == 0 || nc == A->nrows) break;
         L->P = orc_extpi(A, L->strong, L->cf);
+        if (o->interp_trunc > 0 || o->interp_pmax > 0) {
+            ocsr *Pt = orc_truncate(L->P, o->interp_trunc / 1000.0, o->interp_pmax);
+            orc_csr_free(L->P);
+            L->P = Pt;
+        }
         L->R = orc_transpose(L->P);
         A = orc_rap(A, L->P);
         ++l;

@@ -378,6 +378,54 @@ def test_extpi_preserves_constants_and_pattern(oracle_mod):
         assert Ps.data[Ps.indptr[i]] == 1.0
 
 
+@pytest.mark.parametrize("tf,pmax", [(0.0, 0), (0.2, 0), (0.0, 3), (0.3, 4)])
+def test_interpolation_truncation_properties(oracle_mod, tf, pmax):
+    """Truncation keeps what its definition fixes: no row longer than pmax; every kept
+    |w| >= tf max|w| of its row; no dropped weight larger in magnitude than a kept one
+    unless the factor dropped it; row sums unchanged (so constants stay reproduced on a
+    zero-row-sum matrix); tf = 0, pmax = 0 is the identity."""
+    A = _p1_matrix(oracle_mod, 6, dirichlet=False)
+    s = oracle_mod.strength(A, 0.25)
+    cf = oracle_mod.pmis(A, s, 11)
+    P0 = oracle_mod.extpi(A, s, cf).to_scipy()
+    Pt = oracle_mod.truncate(oracle_mod.CSR.from_scipy(P0), tf, pmax).to_scipy()
+    assert Pt.shape == P0.shape
+    if tf == 0.0 and pmax == 0:
+        assert (abs(Pt - P0)).max() == 0.0
+        return
+    assert np.allclose(np.asarray(Pt.sum(axis=1)).ravel(), np.asarray(P0.sum(axis=1)).ravel(), atol=1e-12)
+    has = np.diff(P0.indptr) > 0
+    assert np.allclose(np.asarray(Pt.sum(axis=1)).ravel()[has], 1.0, atol=1e-12)
+    for i in range(P0.shape[0]):
+        c0 = P0.indices[P0.indptr[i]:P0.indptr[i + 1]]
+        w0 = P0.data[P0.indptr[i]:P0.indptr[i + 1]]
+        ct = set(Pt.indices[Pt.indptr[i]:Pt.indptr[i + 1]].tolist())
+        if pmax:
+            assert len(ct) <= pmax
+        if len(w0) == 0:
+            continue
+        mx = np.abs(w0).max()
+        kept = [abs(w) for c, w in zip(c0, w0) if c in ct]
+        dropped = [abs(w) for c, w in zip(c0, w0) if c not in ct and abs(w) >= tf * mx]
+        assert all(k >= tf * mx for k in kept)
+        if kept and dropped:
+            assert max(dropped) <= min(kept)
+
+
+def test_truncation_lowers_operator_complexity_and_converges(oracle_mod):
+    xyz, t = _mesh(6)
+    P = oracle_mod.Problem(xyz, t, 2, kappa_lognormal(t.shape[0], 1))
+    cop, its = [], []
+    for pmax in (0, 4, 2):
+        P.setup(coarse_size=20, interp_pmax=pmax)
+        nnz = [P.level(l)["A"].nnz for l in range(P.levels())]
+        cop.append(sum(nnz) / nnz[0])
+        out = P.solve()
+        assert out["status"] == 0
+        its.append(out["iters"])
+    assert cop[1] <= cop[0] + 1e-12 and cop[2] <= cop[1] + 1e-12, cop
+
+
 def test_rap_matches_dense_product(oracle_mod):
     A = _p1_matrix(oracle_mod, 6)
     s = oracle_mod.strength(A, 0.25)
