@@ -94,7 +94,12 @@ typedef struct {
                              right preconditioning, the outer method of Sec. 6.2; one
                              right-hand side per call) [CG] */
     int restart;          /* FGMRES restart length m, 1..256 [30] */
-    int reserved[4];
+    int interp_pmax;      /* AMG interpolation truncation: keep at most this many weights
+                             per row (0 = no limit) [0] */
+    int interp_trunc;     /* AMG interpolation truncation: drop weights below
+                             (interp_trunc / 1000) x the row's largest |w|, 0..999 [0];
+                             with either, kept weights are scaled to the row's sum */
+    int reserved[2];
 } pkasp_options;
 
 /* Problem sizes after assembly and (for the AMG entries) after setup. */

@@ -30,7 +30,8 @@ class pkasp_options(C.Structure):
                 ("seed", C.c_uint64), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("flexible", C.c_int), ("precond_precision", C.c_int), ("use_graph", C.c_int),
                 ("spmv_threads", C.c_int), ("smoother_layout", C.c_int), ("krylov", C.c_int),
-                ("restart", C.c_int), ("reserved", C.c_int * 4)]
+                ("restart", C.c_int), ("interp_pmax", C.c_int), ("interp_trunc", C.c_int),
+                ("reserved", C.c_int * 2)]
 
 
 class pkasp_info(C.Structure):

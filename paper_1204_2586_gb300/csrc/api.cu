@@ -75,6 +75,8 @@ void pkasp_default_options(pkasp_options *o) {
     o->smoother_layout = 0;
     o->krylov = PKASP_KRYLOV_CG;
     o->restart = 30;
+    o->interp_pmax = 0;
+    o->interp_trunc = 0;
 }
 
 int pkasp_last_error(char *buf, size_t n) {
@@ -245,6 +247,8 @@ int pkasp_setup(pkasp_problem *p, const pkasp_options *opt, pkasp_stream_t strea
     if (o.spmv_threads != 0 && o.spmv_threads != 4 && o.spmv_threads != 8 && o.spmv_threads != 16 &&
         o.spmv_threads != 32)
         return set_error(PKASP_EINVAL, "spmv_threads must be 0, 4, 8, 16 or 32");
+    if (o.interp_pmax < 0 || o.interp_trunc < 0 || o.interp_trunc > 999)
+        return set_error(PKASP_EINVAL, "interp_pmax must be >= 0 and interp_trunc 0..999");
     if (o.krylov != PKASP_KRYLOV_CG && o.krylov != PKASP_KRYLOV_FGMRES)
         return set_error(PKASP_EINVAL, "krylov must be PKASP_KRYLOV_CG or PKASP_KRYLOV_FGMRES");
     if (o.krylov == PKASP_KRYLOV_FGMRES && (o.restart < 1 || o.restart > 256))

@@ -851,7 +851,67 @@ void pmis_device(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_
 
 // One coarsening step on level L: strength, PMIS, ext+i P, R = P^T, A_c = R (A P).
 // Returns false when PMIS keeps no point or every point (the level becomes the coarsest).
-bool coarsen(DevPool &pool, Level &L, double theta, uint64_t pmis_stream, DCSR &Ac, cudaStream_t s) {
+// ---------------------------------------------------------------------------------
+// Interpolation truncation (optional): in every row drop |w| < tf * max|w|, keep the
+// pmax largest |w| of the rest (ties: the lower column), scale the kept weights to the
+// row's original sum. One thread per row; kept entries stay in column order.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ bool trunc_keep(const int32_t *col, const double *val, int64_t lo, int64_t hi,
+                                           int64_t e, double cut, int pmax) {
+    const double a = fabs(val[e]);
+    if (a < cut) return false;
+    if (pmax <= 0) return true;
+    int rank = 0;  // candidates ahead of e: larger |w|, or equal |w| and a lower column
+    for (int64_t f = lo; f < hi; ++f) {
+        const double b = fabs(val[f]);
+        if (b < cut || f == e) continue;
+        if (b > a || (b == a && col[f] < col[e])) ++rank;
+    }
+    return rank < pmax;
+}
+
+__global__ void k_trunc_count(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                              const double *__restrict__ val, double tf, int pmax, int64_t *__restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t lo = ptr[i], hi = ptr[i + 1];
+    double mx = 0.0;
+    for (int64_t e = lo; e < hi; ++e) mx = fmax(mx, fabs(val[e]));
+    const double cut = tf > 0.0 ? tf * mx : -1.0;
+    int64_t c = 0;
+    for (int64_t e = lo; e < hi; ++e) c += trunc_keep(col, val, lo, hi, e, cut, pmax);
+    cnt[i] = c;
+}
+
+__global__ void k_trunc_fill(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                             const double *__restrict__ val, double tf, int pmax, const int64_t *__restrict__ optr,
+                             int32_t *__restrict__ ocol, double *__restrict__ oval) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t lo = ptr[i], hi = ptr[i + 1];
+    double mx = 0.0, sum = 0.0;
+    for (int64_t e = lo; e < hi; ++e) {
+        mx = fmax(mx, fabs(val[e]));
+        sum += val[e];
+    }
+    const double cut = tf > 0.0 ? tf * mx : -1.0;
+    int64_t o = optr[i];
+    double kept = 0.0;
+    for (int64_t e = lo; e < hi; ++e)
+        if (trunc_keep(col, val, lo, hi, e, cut, pmax)) {
+            ocol[o] = col[e];
+            oval[o] = val[e];
+            kept += val[e];
+            ++o;
+        }
+    if (o - optr[i] < hi - lo && kept != 0.0) {
+        const double scale = sum / kept;
+        for (int64_t q = optr[i]; q < o; ++q) oval[q] *= scale;
+    }
+}
+
+bool coarsen(DevPool &pool, Level &L, double theta, uint64_t pmis_stream, DCSR &Ac, cudaStream_t s,
+             double trunc_factor, int pmax) {
     const DCSR &A = L.A;
     const int64_t n = A.n;
     L.strong = pool.get<uint8_t>(A.nnz > 0 ? A.nnz : 1);
@@ -882,11 +942,28 @@ bool coarsen(DevPool &pool, Level &L, double theta, uint64_t pmis_stream, DCSR &
             PK_LAUNCH();
             exclusive_scan(cnt, n, s);
             int64_t pnnz = read_i64(cnt + n, s);
-            dcsr_alloc(pool, L.P, n, nc, pnnz);
-            PK_CUDA(cudaMemcpyAsync(L.P.ptr, cnt, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+            const bool trunc = trunc_factor > 0.0 || pmax > 0;
+            DCSR full;  // ext+i before truncation (scratch when truncating)
+            dcsr_alloc(trunc ? tmp : pool, full, n, nc, pnnz);
+            PK_CUDA(cudaMemcpyAsync(full.ptr, cnt, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
             k_extpi_fill<<<blocks_for(n, 128), 128, 0, s>>>(n, A.ptr, A.col, A.val, L.strong, L.cf, cidx, ub, scr,
-                                                            L.P.ptr, L.P.col, L.P.val);
+                                                            full.ptr, full.col, full.val);
             PK_LAUNCH();
+            if (trunc) {
+                int64_t *tc = tmp.get<int64_t>(n + 1);
+                k_trunc_count<<<blocks_for(n, 256), 256, 0, s>>>(n, full.ptr, full.col, full.val, trunc_factor, pmax,
+                                                                 tc);
+                PK_LAUNCH();
+                exclusive_scan(tc, n, s);
+                const int64_t tnnz = read_i64(tc + n, s);
+                dcsr_alloc(pool, L.P, n, nc, tnnz);
+                PK_CUDA(cudaMemcpyAsync(L.P.ptr, tc, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+                k_trunc_fill<<<blocks_for(n, 256), 256, 0, s>>>(n, full.ptr, full.col, full.val, trunc_factor, pmax,
+                                                                L.P.ptr, L.P.col, L.P.val);
+                PK_LAUNCH();
+            } else {
+                L.P = full;
+            }
             PK_CUDA(cudaStreamSynchronize(s));
             transpose(pool, L.P, L.R, s);
             DCSR AP;
