@@ -221,7 +221,7 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD["name"],
-                    choices=[WORKLOAD["name"], P4["name"], BATCHED["name"], "theta_study"])
+                    choices=[WORKLOAD["name"], P4["name"], BATCHED["name"], "theta_study", "cop_study"])
     ap.add_argument("--smoother-layout", type=int, default=0,
                     help="pin the fine smoother layout (pkasp_options.smoother_layout) instead of "
                          "autotuning it; for profiler runs, under which the autotuner's timings "
@@ -256,6 +256,9 @@ def main():
     build.build()
     if args.workload == "theta_study":
         run_theta_study(args)
+        return
+    if args.workload == "cop_study":
+        run_cop_study(args)
         return
     if args.workload == BATCHED["name"]:
         run_batched(args, ws, rank, local)
@@ -461,6 +464,51 @@ def run_theta_study(args):
                              "levels": int(info.levels), "op_complexity": info.op_complexity})
         G.close()
     print(json.dumps({"study": "theta", "tol": 1e-8, "krylov": "PCG", "rows": rows}))
+
+
+def run_cop_study(args):
+    """Operator complexities against the paper's Table 6 (PMIS + extended+i, theta 0.25):
+    plain AMG on A_h (sum nnz(A_l) / nnz(A_h)), the P1 AMG of the auxiliary space
+    (relative to A_H) and the whole auxiliary-space hierarchy relative to A_h ("GAMG":
+    (nnz(A_h) + sum nnz of the P1 levels) / nnz(A_h)); without truncation and with at most
+    4 interpolation weights per row. Iterations and times beside them. One JSON line."""
+    import torch
+
+    from paper_1204_2586_gb300 import Problem
+    from paper_1204_2586_gb300.inputs import kuhn_mesh
+
+    rows = []
+    for k, n in THETA_STUDY:
+        xyz, t = kuhn_mesh(n, 0.2, 0)
+        G = Problem(xyz, t, k)
+        b = G.rhs()
+        nnz_h = int(G.info.nnz_h)
+        for pmax in (0, 4):
+            for mode, name in ((0, "aux_space_additive"), (2, "plain_amg")):
+                t0 = time.perf_counter()
+                G.setup(theta=0.25, mode=mode, level_smoother=LEVEL_SMOOTHER, interp_pmax=pmax, max_iter=2000)
+                torch.cuda.synchronize()
+                setup_s = time.perf_counter() - t0
+                x = torch.zeros_like(b)
+                G.solve(b, x, raise_on_fail=False)
+                x.zero_()
+                _, st = G.solve(b, x, raise_on_fail=False)
+                info = G.info
+                lev_nnz = [int(info.level_nnz[l]) for l in range(info.levels)]
+                row = {"k": k, "n": n, "n_h": G.nh, "interp_pmax": pmax, "method": name,
+                       "iterations": st["iters"][0], "solve_s": st["solve_ms"] / 1e3, "setup_s": setup_s,
+                       "levels": int(info.levels)}
+                if mode == 2:
+                    row["cop_amg_on_Ah"] = sum(lev_nnz) / lev_nnz[0]
+                else:
+                    row["cop_p1_amg"] = sum(lev_nnz) / lev_nnz[0]
+                    row["cop_gamg_rel_Ah"] = (nnz_h + sum(lev_nnz)) / nnz_h
+                rows.append(row)
+        G.close()
+    print(json.dumps({"study": "operator_complexity", "theta": 0.25, "rows": rows,
+                      "paper_table6": {"P2": {"AMG": 1.67, "P1-AMG": 1.76, "GAMG": 1.12},
+                                       "P3": {"AMG": 1.56, "P1-AMG": 1.96, "GAMG": 1.02},
+                                       "P4": {"AMG": 1.36, "P1-AMG": 1.70, "GAMG": 1.01}}}))
 
 
 def run_batched(args, ws, rank, local):
