@@ -139,6 +139,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def replica_totals(ms, work, device="cuda"):
+    """Whole-job figures of independent replicas (one per rank): the slowest rank's time
+    and the work of all ranks summed. A single process returns its own figures."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(ms), float(work)
+    t = torch.tensor([float(ms), float(work)], dtype=torch.float64, device=device)
+    mx = t[:1].clone()
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    sm = t[1:].clone()
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return float(mx.item()), float(sm.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -304,12 +319,8 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     nh = G.nh
-    work = nh * sum(iters) * ws
+    ms, work = replica_totals(ms, nh * sum(iters))
     value = work / (ms / 1e3) / 1e6
     sol_s = ms / 1e3 / args.steps
 
@@ -329,7 +340,8 @@ def main():
         _, st = G.solve(bnp, xnp)
         e_iters.append(st["iters"][0])
     e2e_s = time.perf_counter() - t0
-    e2e_value = nh * sum(e_iters) * ws / e2e_s / 1e6
+    e2e_ms, e2e_work = replica_totals(e2e_s * 1e3, nh * sum(e_iters))
+    e2e_value = e2e_work / (e2e_ms / 1e3) / 1e6
 
     # Rooflines, measured with CUDA events on the launching stream (pkasp_time_kernel).
     # Dominant kernel by the launch list of a solve (profiles/launches_p3_n32_solve.md):
@@ -568,11 +580,8 @@ def run_batched(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nh * sum(col_iters) * ws / (ms / 1e3) / 1e6
+    ms, work = replica_totals(ms, nh * sum(col_iters))
+    value = work / (ms / 1e3) / 1e6
     sol_s = ms / 1e3 / args.steps
     info = G.info
     max_true_rel = max(st["true_rel"])
@@ -593,7 +602,8 @@ def run_batched(args, ws, rank, local):
         _, st = G.solve(bnp, xnp)
         e_iters.append(sum(st["iters"]))
     e2e_s = time.perf_counter() - t0
-    e2e_value = nh * sum(e_iters) * ws / e2e_s / 1e6
+    e2e_ms, e2e_work = replica_totals(e2e_s * 1e3, nh * sum(e_iters))
+    e2e_value = e2e_work / (e2e_ms / 1e3) / 1e6
 
     # roofline of the dominant kernel, the blocked FP64 SpMM Q = A_h P with its per-column
     # dot (P, Q): 48 FP64 FMA per stored entry and column, so it is bound by the FP64 pipe
