@@ -106,6 +106,17 @@ def lib():
     L.orc_solve.argtypes = [vp, f64p, f64p, f64p, C.c_int, C.POINTER(C.c_int),
                             C.POINTER(C.c_double)]
     L.orc_grad_kappa.argtypes = [vp, f64p, f64p, f64p]
+    L.orc_stokes_create.restype = vp
+    L.orc_stokes_create.argtypes = [vp, vp, C.c_int]
+    L.orc_stokes_free.argtypes = [vp]
+    L.orc_stokes_sizes.argtypes = [vp, i64p]
+    L.orc_stokes_matrix.restype = vp
+    L.orc_stokes_matrix.argtypes = [vp, C.c_int]
+    L.orc_stokes_apply.argtypes = [vp, f64p, f64p]
+    L.orc_stokes_prec.argtypes = [vp, f64p, f64p]
+    L.orc_stokes_solve.restype = C.c_int
+    L.orc_stokes_solve.argtypes = [vp, f64p, f64p, C.c_int, C.c_double, C.c_int, f64p, C.c_int,
+                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.orc_l2_error_sine.restype = C.c_double
     L.orc_l2_error_sine.argtypes = [vp, f64p]
     _lib = L
@@ -422,3 +433,50 @@ class Problem:
 
     def l2_error_sine(self, u):
         return float(lib().orc_l2_error_sine(self.h, _f64(u)))
+
+
+class Stokes:
+    """Taylor-Hood P_k - P_{k-1} Stokes system (Sec. 5) over two oracle problems on one
+    mesh: ``u`` of degree k with Dirichlet nodes removed (set up: its auxiliary-space
+    preconditioner approximates A^{-1}) and ``p`` of degree k-1 created with
+    ``dirichlet=False``. Unknowns: 3 velocity components (component-major), then p."""
+
+    def __init__(self, u: "Problem", p: "Problem", mp_iters: int = 10):
+        self.u, self.p = u, p
+        h = lib().orc_stokes_create(u.h, p.h, int(mp_iters))
+        if not h:
+            raise ValueError("Stokes needs a degree-k Dirichlet velocity problem and a degree-(k-1) "
+                             "pressure problem without Dirichlet nodes on the same mesh")
+        self.h = h
+        sz = np.zeros(3, np.int64)
+        lib().orc_stokes_sizes(h, sz)
+        self.nh, self.np, self.n = (int(v) for v in sz)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_stokes_free(self.h)
+            self.h = None
+
+    def matrix(self, which):
+        """0: B (n_p x 3 n_h), 1: B^T, 2: M_p."""
+        return CSR.from_handle(lib().orc_stokes_matrix(self.h, which))
+
+    def apply(self, x):
+        y = np.zeros(self.n)
+        lib().orc_stokes_apply(self.h, _f64(x), y)
+        return y
+
+    def prec(self, r):
+        z = np.zeros(self.n)
+        lib().orc_stokes_prec(self.h, _f64(r), z)
+        return z
+
+    def solve(self, b, x0=None, restart=30, tol=1e-8, max_iter=1000, hist_cap=2048):
+        x = np.zeros(self.n) if x0 is None else _f64(x0).copy()
+        hist = np.zeros(hist_cap)
+        it = C.c_int(0)
+        tr = C.c_double(0)
+        st = lib().orc_stokes_solve(self.h, _f64(b), x, int(restart), float(tol), int(max_iter), hist,
+                                    hist_cap, C.byref(it), C.byref(tr))
+        n = min(it.value + 1, hist_cap)
+        return dict(x=x, status=int(st), iters=int(it.value), hist=hist[:n].copy(), true_rel=float(tr.value))

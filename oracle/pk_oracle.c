@@ -1698,10 +1698,12 @@ void orc_apply_prec(oproblem *P, const double *r, double *z) {
  *      then restart from the true residual until converged. A zero h_{j+1,j} ends the
  *      cycle (the Krylov space holds the solution).
  * ---------------------------------------------------------------------------------- */
-int orc_fgmres(oproblem *P, const double *b, double *x, double *hist, int hist_cap,
-               int *iters_out, double *true_rel_out) {
-    const int64_t n = P->nh;
-    const int m = P->o.restart > 0 ? P->o.restart : 30;
+typedef void (*orc_apply_fn)(void *ctx, const double *x, double *y);
+
+static int fgmres_core(int64_t n, orc_apply_fn op, orc_apply_fn prec, void *ctx, int restart, double tol,
+                       int max_iter, const double *b, double *x, double *hist, int hist_cap, int *iters_out,
+                       double *true_rel_out) {
+    const int m = restart > 0 ? restart : 30;
     double *V = (double *)xmalloc(sizeof(double) * (size_t)n * (size_t)(m + 1));
     double *Z = (double *)xmalloc(sizeof(double) * (size_t)n * (size_t)m);
     double *w = (double *)xmalloc(sizeof(double) * (size_t)n);
@@ -1712,7 +1714,7 @@ int orc_fgmres(oproblem *P, const double *b, double *x, double *hist, int hist_c
     double *y = (double *)xmalloc(sizeof(double) * (size_t)m);
     double *hc = (double *)xmalloc(sizeof(double) * (size_t)(m + 1));
     int it = 0, status = 1;
-    orc_spmv(P->Ah, x, w);
+    op(ctx, x, w);
     for (int64_t i = 0; i < n; ++i) V[i] = b[i] - w[i];
     const double r0 = sqrt(dot(n, V, V));
     if (hist && hist_cap > 0) hist[0] = r0;
@@ -1724,10 +1726,10 @@ int orc_fgmres(oproblem *P, const double *b, double *x, double *hist, int hist_c
         g[0] = beta;
         int k = 0; /* Arnoldi steps of this cycle */
         int converged = 0;
-        for (int j = 0; j < m && it < P->o.max_iter; ++j) {
+        for (int j = 0; j < m && it < max_iter; ++j) {
             double *vj = V + (size_t)j * (size_t)n, *zj = Z + (size_t)j * (size_t)n;
-            orc_apply_prec(P, vj, zj);
-            orc_spmv(P->Ah, zj, w);
+            prec(ctx, vj, zj);
+            op(ctx, zj, w);
             for (int i = 0; i <= j; ++i) H[i * m + j] = 0.0;
             for (int pass = 0; pass < 2; ++pass) {
                 for (int i = 0; i <= j; ++i) hc[i] = dot(n, w, V + (size_t)i * (size_t)n);
@@ -1760,7 +1762,7 @@ int orc_fgmres(oproblem *P, const double *b, double *x, double *hist, int hist_c
             k = j + 1;
             const double est = fabs(g[j + 1]);
             if (hist && it < hist_cap) hist[it] = est;
-            if (est <= P->o.tol * r0 || hn == 0.0) {
+            if (est <= tol * r0 || hn == 0.0) {
                 converged = 1;
                 break;
             }
@@ -1776,14 +1778,14 @@ int orc_fgmres(oproblem *P, const double *b, double *x, double *hist, int hist_c
             for (int64_t q = 0; q < n; ++q) x[q] += y[l] * zl[q];
         }
         /* restart from the true residual */
-        orc_spmv(P->Ah, x, w);
+        op(ctx, x, w);
         for (int64_t i = 0; i < n; ++i) V[i] = b[i] - w[i];
         beta = sqrt(dot(n, V, V));
-        if (beta <= P->o.tol * r0) {
+        if (beta <= tol * r0) {
             status = 0;
             break;
         }
-        if (it >= P->o.max_iter) break;
+        if (it >= max_iter) break;
         (void)converged;
     }
     if (true_rel_out) *true_rel_out = r0 > 0.0 ? beta / r0 : 0.0;
@@ -1798,6 +1800,15 @@ int orc_fgmres(oproblem *P, const double *b, double *x, double *hist, int hist_c
     free(y);
     free(hc);
     return status;
+}
+
+static void poisson_op(void *ctx, const double *x, double *y) { orc_spmv(((oproblem *)ctx)->Ah, x, y); }
+static void poisson_prec(void *ctx, const double *r, double *z) { orc_apply_prec((oproblem *)ctx, r, z); }
+
+int orc_fgmres(oproblem *P, const double *b, double *x, double *hist, int hist_cap, int *iters_out,
+               double *true_rel_out) {
+    return fgmres_core(P->nh, poisson_op, poisson_prec, P, P->o.restart, P->o.tol, P->o.max_iter, b, x, hist,
+                       hist_cap, iters_out, true_rel_out);
 }
 
 int orc_solve(oproblem *P, const double *b, double *x, double *hist, int hist_cap,
@@ -1871,6 +1882,268 @@ int orc_solve(oproblem *P, const double *b, double *x, double *hist, int hist_ca
     free(q);
     free(rold);
     return status;
+}
+
+/* ------------------------------------------------------------------------------------
+ * 14. Stokes with Taylor-Hood P_k - P_{k-1} elements (Sec. 5): F = [A B^T; B 0] with A
+ *     the block diagonal of three copies of the Dirichlet P_k Laplacian A_h (velocity
+ *     unknowns component-major: component c, unknown j -> c n_h + j), B the discrete
+ *     divergence -div_h: B_{q,(c,j)} = -int psi_q d_c phi_j (pressure on all P_{k-1}
+ *     nodes), M_p the pressure mass matrix. The block upper-triangular preconditioner
+ *     Q_t = [A B^T; 0 -S]^{-1} (Eq. 5.4) with A^{-1} ~ the auxiliary-space preconditioner
+ *     per component and S ~ M_p, solved by mp_iters steps of CG with the diagonal of M_p
+ *     as preconditioner:  z_p = -M_p^{-1} r_p,  z_u = B_aux (r_u - B^T z_p).
+ *     Element integrals exactly by monomial integration on the reference tetrahedron.
+ * ---------------------------------------------------------------------------------- */
+struct ostokes {
+    oproblem *U, *P;  /* velocity space (degree k, Dirichlet), pressure space (k-1, all nodes) */
+    int64_t nh, np, n;
+    ocsr *B, *BT, *M;
+    double *mdiag;
+    int mp_iters;
+};
+
+/* psi_m of degree k as monomials in lambda: coefficient prod_a c_a(e_a) */
+static void phi_terms(int k, const int32_t *m, dterms *t) {
+    double cf[4][8];
+    for (int b = 0; b < 4; ++b) lag_factor(k, m[b], cf[b]);
+    t->n = 0;
+    for (int e0 = 0; e0 <= m[0]; ++e0)
+        for (int e1 = 0; e1 <= m[1]; ++e1)
+            for (int e2 = 0; e2 <= m[2]; ++e2)
+                for (int e3 = 0; e3 <= m[3]; ++e3) {
+                    int ee[4] = {e0, e1, e2, e3};
+                    double c = 1.0;
+                    for (int b = 0; b < 4; ++b) c *= cf[b][ee[b]];
+                    if (c == 0.0) continue;
+                    int q = t->n++;
+                    for (int b = 0; b < 4; ++b) t->e[q][b] = ee[b];
+                    t->c[q] = c;
+                }
+}
+
+static double term_product_integral(const dterms *a, const dterms *b) {
+    double s = 0.0;
+    for (int p = 0; p < a->n; ++p)
+        for (int q = 0; q < b->n; ++q) {
+            int g[4];
+            for (int c = 0; c < 4; ++c) g[c] = a->e[p][c] + b->e[q][c];
+            s += a->c[p] * b->c[q] * mono_int(g);
+        }
+    return s;
+}
+
+/* gradients of the barycentric coordinates (rows) and |T| */
+static double tet_grads(const double *x, double gl[4][3]) {
+    double J[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) J[r][c] = x[3 * (c + 1) + r] - x[r];
+    double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                 J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                 J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    double inv[3][3];
+    inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    for (int c = 0; c < 3; ++c) {
+        gl[1][c] = inv[0][c];
+        gl[2][c] = inv[1][c];
+        gl[3][c] = inv[2][c];
+        gl[0][c] = -(inv[0][c] + inv[1][c] + inv[2][c]);
+    }
+    return det / 6.0;
+}
+
+typedef struct {
+    int64_t r, c, seq;
+    double v;
+} otrip;
+
+static int cmp_trip(const void *a, const void *b) {
+    const otrip *x = (const otrip *)a, *y = (const otrip *)b;
+    if (x->r != y->r) return x->r < y->r ? -1 : 1;
+    if (x->c != y->c) return x->c < y->c ? -1 : 1;
+    return x->seq < y->seq ? -1 : (x->seq > y->seq);
+}
+
+/* CSR from triplets; duplicates summed in the order they were added */
+static ocsr *csr_from_trips(otrip *t, int64_t nt, int64_t nrows, int64_t ncols) {
+    qsort(t, (size_t)nt, sizeof(otrip), cmp_trip);
+    int64_t *ptr = (int64_t *)xcalloc((size_t)nrows + 1, sizeof(int64_t));
+    int32_t *col = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(nt ? nt : 1));
+    double *val = (double *)xmalloc(sizeof(double) * (size_t)(nt ? nt : 1));
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < nt;) {
+        int64_t j = i;
+        double s = 0.0;
+        while (j < nt && t[j].r == t[i].r && t[j].c == t[i].c) s += t[j++].v;
+        col[nnz] = (int32_t)t[i].c;
+        val[nnz] = s;
+        ++nnz;
+        ptr[t[i].r + 1]++;
+        i = j;
+    }
+    for (int64_t r = 0; r < nrows; ++r) ptr[r + 1] += ptr[r];
+    ocsr *a = orc_csr_new(nrows, ncols, nnz, ptr, col, val);
+    free(ptr);
+    free(col);
+    free(val);
+    return a;
+}
+
+ostokes *orc_stokes_create(oproblem *U, oproblem *Pp, int mp_iters) {
+    if (!U || !Pp || U->k < 2 || Pp->k != U->k - 1 || Pp->dirichlet || U->nt != Pp->nt) return NULL;
+    ostokes *S = (ostokes *)xcalloc(1, sizeof(ostokes));
+    S->U = U;
+    S->P = Pp;
+    S->nh = U->nh;
+    S->np = Pp->nh;
+    S->n = 3 * S->nh + S->np;
+    S->mp_iters = mp_iters;
+    const int nu = U->nloc, npl = Pp->nloc;
+    /* reference tensors: R[a][m][n] = (1/|T|) int psi_m dphi_n/dlambda_a,
+       Mr[m][m'] = (1/|T|) int psi_m psi_m' */
+    dterms *tp = (dterms *)xmalloc(sizeof(dterms) * (size_t)npl);
+    dterms *tu = (dterms *)xmalloc(sizeof(dterms) * 4 * (size_t)nu);
+    for (int m = 0; m < npl; ++m) phi_terms(Pp->k, Pp->mi[m], &tp[m]);
+    for (int n = 0; n < nu; ++n)
+        for (int a = 0; a < 4; ++a) dphi_terms(U->k, U->mi[n], a, &tu[n * 4 + a]);
+    double *R = (double *)xmalloc(sizeof(double) * 4 * (size_t)npl * (size_t)nu);
+    double *Mr = (double *)xmalloc(sizeof(double) * (size_t)npl * (size_t)npl);
+    for (int a = 0; a < 4; ++a)
+        for (int m = 0; m < npl; ++m)
+            for (int n = 0; n < nu; ++n) R[(a * npl + m) * nu + n] = term_product_integral(&tp[m], &tu[n * 4 + a]);
+    for (int m = 0; m < npl; ++m)
+        for (int q = 0; q < npl; ++q) Mr[m * npl + q] = term_product_integral(&tp[m], &tp[q]);
+    int64_t capB = U->nt * (int64_t)npl * 3 * nu, capM = U->nt * (int64_t)npl * npl;
+    otrip *tb = (otrip *)xmalloc(sizeof(otrip) * (size_t)capB);
+    otrip *tm = (otrip *)xmalloc(sizeof(otrip) * (size_t)capM);
+    int64_t nb = 0, nm = 0;
+    for (int64_t t = 0; t < U->nt; ++t) {
+        double x[12], gl[4][3];
+        for (int v = 0; v < 4; ++v)
+            for (int c = 0; c < 3; ++c) x[3 * v + c] = U->xyz[3 * (int64_t)U->tets[4 * t + v] + c];
+        const double vol = tet_grads(x, gl);
+        for (int m = 0; m < npl; ++m) {
+            const int64_t q = Pp->elem_dof[t * npl + m];
+            for (int n = 0; n < nu; ++n) {
+                const int64_t j = U->elem_dof[t * nu + n];
+                if (j < 0) continue;
+                for (int c = 0; c < 3; ++c) {
+                    double s = 0.0;
+                    for (int a = 0; a < 4; ++a) s += gl[a][c] * R[(a * npl + m) * nu + n];
+                    tb[nb] = (otrip){q, c * S->nh + j, nb, -vol * s};
+                    ++nb;
+                }
+            }
+            for (int m2 = 0; m2 < npl; ++m2) {
+                tm[nm] = (otrip){q, Pp->elem_dof[t * npl + m2], nm, vol * Mr[m * npl + m2]};
+                ++nm;
+            }
+        }
+    }
+    S->B = csr_from_trips(tb, nb, S->np, 3 * S->nh);
+    S->M = csr_from_trips(tm, nm, S->np, S->np);
+    S->BT = orc_transpose(S->B);
+    S->mdiag = (double *)xmalloc(sizeof(double) * (size_t)S->np);
+    for (int64_t i = 0; i < S->np; ++i)
+        for (int64_t e = S->M->ptr[i]; e < S->M->ptr[i + 1]; ++e)
+            if (S->M->col[e] == i) S->mdiag[i] = S->M->val[e];
+    free(tb);
+    free(tm);
+    free(R);
+    free(Mr);
+    free(tp);
+    free(tu);
+    return S;
+}
+
+void orc_stokes_free(ostokes *S) {
+    if (!S) return;
+    orc_csr_free(S->B);
+    orc_csr_free(S->BT);
+    orc_csr_free(S->M);
+    free(S->mdiag);
+    free(S);
+}
+
+void orc_stokes_sizes(const ostokes *S, int64_t *out3) {
+    out3[0] = S->nh;
+    out3[1] = S->np;
+    out3[2] = S->n;
+}
+
+const ocsr *orc_stokes_matrix(const ostokes *S, int which) {
+    return which == 0 ? S->B : which == 1 ? S->BT : S->M;
+}
+
+/* y = F x */
+void orc_stokes_apply(ostokes *S, const double *x, double *y) {
+    const int64_t nh = S->nh, nu = 3 * nh;
+    double *t = (double *)xmalloc(sizeof(double) * (size_t)(nu ? nu : 1));
+    for (int c = 0; c < 3; ++c) orc_spmv(S->U->Ah, x + c * nh, y + c * nh);
+    orc_spmv(S->BT, x + nu, t);
+    for (int64_t i = 0; i < nu; ++i) y[i] += t[i];
+    orc_spmv(S->B, x, y + nu);
+    free(t);
+}
+
+/* z = Q_t r */
+void orc_stokes_prec(ostokes *S, const double *r, double *z) {
+    const int64_t nh = S->nh, nu = 3 * nh, np = S->np;
+    double *xp = (double *)xcalloc((size_t)(np ? np : 1), sizeof(double));
+    double *rr = (double *)xmalloc(sizeof(double) * (size_t)(np ? np : 1));
+    double *zz = (double *)xmalloc(sizeof(double) * (size_t)(np ? np : 1));
+    double *pp = (double *)xmalloc(sizeof(double) * (size_t)(np ? np : 1));
+    double *qq = (double *)xmalloc(sizeof(double) * (size_t)(np ? np : 1));
+    /* M_p x = r_p by CG with the diagonal of M_p, mp_iters steps from zero */
+    for (int64_t i = 0; i < np; ++i) {
+        rr[i] = r[nu + i];
+        zz[i] = rr[i] / S->mdiag[i];
+        pp[i] = zz[i];
+    }
+    double rho = dot(np, rr, zz);
+    for (int it = 0; it < S->mp_iters && rho != 0.0; ++it) {
+        orc_spmv(S->M, pp, qq);
+        const double alpha = rho / dot(np, pp, qq);
+        for (int64_t i = 0; i < np; ++i) {
+            xp[i] += alpha * pp[i];
+            rr[i] -= alpha * qq[i];
+            zz[i] = rr[i] / S->mdiag[i];
+        }
+        const double rho2 = dot(np, rr, zz);
+        const double beta = rho2 / rho;
+        rho = rho2;
+        for (int64_t i = 0; i < np; ++i) pp[i] = zz[i] + beta * pp[i];
+    }
+    for (int64_t i = 0; i < np; ++i) z[nu + i] = -xp[i];
+    /* z_u = B_aux (r_u - B^T z_p), component by component */
+    double *t = (double *)xmalloc(sizeof(double) * (size_t)(nu ? nu : 1));
+    orc_spmv(S->BT, z + nu, t);
+    for (int64_t i = 0; i < nu; ++i) t[i] = r[i] - t[i];
+    for (int c = 0; c < 3; ++c) orc_apply_prec(S->U, t + c * nh, z + c * nh);
+    free(t);
+    free(xp);
+    free(rr);
+    free(zz);
+    free(pp);
+    free(qq);
+}
+
+static void stokes_op(void *ctx, const double *x, double *y) { orc_stokes_apply((ostokes *)ctx, x, y); }
+static void stokes_pc(void *ctx, const double *r, double *z) { orc_stokes_prec((ostokes *)ctx, r, z); }
+
+/* FGMRES(restart) on F x = b with Q_t (the velocity preconditioner needs orc_setup on U) */
+int orc_stokes_solve(ostokes *S, const double *b, double *x, int restart, double tol, int max_iter, double *hist,
+                     int hist_cap, int *iters_out, double *true_rel_out) {
+    return fgmres_core(S->n, stokes_op, stokes_pc, S, restart, tol, max_iter, b, x, hist, hist_cap, iters_out,
+                       true_rel_out);
 }
 
 /* ------------------------------------------------------------------------------------

@@ -92,6 +92,19 @@ int orc_fgmres(oproblem *p, const double *b, double *x, double *hist, int hist_c
 int orc_solve(oproblem *p, const double *b, double *x, double *hist, int hist_cap,
               int *iters_out, double *true_rel_out);
 void orc_grad_kappa(const oproblem *p, const double *u, const double *lam, double *g);
+
+/* Stokes, Taylor-Hood P_k - P_{k-1} (Sec. 5): u (degree k, Dirichlet), p (degree k-1,
+ * created with dirichlet = 0) on the same mesh; M_p solved by mp_iters diagonal-PCG
+ * steps inside the block upper-triangular preconditioner Q_t. */
+typedef struct ostokes ostokes;
+ostokes *orc_stokes_create(oproblem *u, oproblem *p, int mp_iters);
+void orc_stokes_free(ostokes *s);
+void orc_stokes_sizes(const ostokes *s, int64_t *out3); /* n_h, n_p, 3 n_h + n_p */
+const ocsr *orc_stokes_matrix(const ostokes *s, int which); /* 0 B, 1 B^T, 2 M_p */
+void orc_stokes_apply(ostokes *s, const double *x, double *y);
+void orc_stokes_prec(ostokes *s, const double *r, double *z);
+int orc_stokes_solve(ostokes *s, const double *b, double *x, int restart, double tol, int max_iter,
+                     double *hist, int hist_cap, int *iters_out, double *true_rel_out);
 double orc_l2_error_sine(const oproblem *p, const double *u);
 
 #ifdef __cplusplus

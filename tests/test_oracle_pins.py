@@ -675,6 +675,91 @@ def test_theta_robustness(oracle_mod):
     assert max(its) - min(its) <= 3, its
 
 
+# ---------------------------------------------------------------------------------
+# Stokes, Taylor-Hood P_k - P_{k-1} (Sec. 5)
+# ---------------------------------------------------------------------------------
+def _stokes(oracle_mod, k, n, setup=True, **kw):
+    xyz, t = _mesh(n)
+    U = oracle_mod.Problem(xyz, t, k)
+    if setup:
+        U.setup(**kw)
+    Pp = oracle_mod.Problem(xyz, t, k - 1, dirichlet=False)
+    return xyz, t, U, Pp, oracle_mod.Stokes(U, Pp)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_stokes_gradient_of_linear_pressure(oracle_mod, k):
+    """B = -div_h: for the pressure q = x_c (exact in P_{k-1}), integration by parts with
+    phi = 0 on the boundary gives (B^T q)_{(d, v)} = delta_cd int phi_v. int phi_v is
+    computed here by Grundmann-Moeller quadrature of the basis on every element."""
+    xyz, t, U, Pp, S = _stokes(oracle_mod, k, 2, setup=False)
+    BT = S.matrix(1).to_scipy()
+    _, pxyz = Pp.dofs()
+    lam, w = oracle_mod.gm_rule(k)
+    phi = np.array([oracle_mod.basis_eval(k, l) for l in lam])  # [q, nloc]
+    ref = 6.0 * (w @ phi)  # (1/|T|) int phi_m; the rule's weights sum to the reference volume 1/6
+    ed = U.elem_dofs()
+    integ = np.zeros(S.nh)
+    for e in range(t.shape[0]):
+        X = xyz[t[e]]
+        vol = abs(np.linalg.det((X[1:] - X[0]).T)) / 6.0
+        for m in range(ed.shape[1]):
+            if ed[e, m] >= 0:
+                integ[ed[e, m]] += vol * ref[m]
+    for c in range(3):
+        y = BT @ pxyz[:, c]
+        for d in range(3):
+            want = integ if d == c else np.zeros(S.nh)
+            assert np.abs(y[d * S.nh:(d + 1) * S.nh] - want).max() <= 1e-12 * np.abs(integ).max(), (c, d)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_stokes_pressure_mass_matrix_integrates_exactly(oracle_mod, k):
+    _, _, _, Pp, S = _stokes(oracle_mod, k, 2, setup=False)
+    M = S.matrix(2).to_scipy()
+    _, pxyz = Pp.dofs()
+    one = np.ones(S.np)
+    assert abs(one @ M @ one - 1.0) <= 1e-13            # |unit cube|
+    assert abs(pxyz[:, 0] @ M @ pxyz[:, 0] - 1.0 / 3.0) <= 1e-13  # int x^2
+    assert abs(pxyz[:, 0] @ M @ pxyz[:, 1] - 0.25) <= 1e-13      # int x y
+    assert (abs(M - M.T)).max() <= 1e-15
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_stokes_solve_matches_dense_solution(oracle_mod, k):
+    """F x = b with b_p = 0 is consistent (F is singular only in the constant pressure):
+    FGMRES with Q_t reaches the dense least-squares solution; velocity exactly, pressure
+    up to a constant; the discrete velocity is divergence free (B u = 0)."""
+    _, _, U, Pp, S = _stokes(oracle_mod, k, 2, coarse_size=5)
+    rng = np.random.default_rng(3)
+    b = np.concatenate([rng.standard_normal(3 * S.nh), np.zeros(S.np)])
+    out = S.solve(b, tol=1e-12, max_iter=500)
+    assert out["status"] == 0
+    A = U.matrix(0).to_scipy().toarray()
+    B = S.matrix(0).to_scipy().toarray()
+    F = np.block([[sla.block_diag(A, A, A), B.T], [B, np.zeros((S.np, S.np))]])
+    xd, *_ = np.linalg.lstsq(F, b, rcond=None)
+    nu = 3 * S.nh
+    u, p = out["x"][:nu], out["x"][nu:]
+    assert np.linalg.norm(u - xd[:nu]) <= 1e-9 * np.linalg.norm(xd[:nu])
+    dp = (p - p.mean()) - (xd[nu:] - xd[nu:].mean())
+    assert np.linalg.norm(dp) <= 1e-8 * np.linalg.norm(xd[nu:] - xd[nu:].mean())
+    assert np.linalg.norm(B @ u) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_stokes_iterations_flat_in_h(oracle_mod):
+    """Q_t with one auxiliary-space cycle per velocity component (Sec. 6.3: the iteration
+    count does not grow with the number of unknowns)."""
+    its = []
+    for n in (3, 6):
+        _, _, U, Pp, S = _stokes(oracle_mod, 2, n, coarse_size=20)
+        b = np.concatenate([np.random.default_rng(1).standard_normal(3 * S.nh), np.zeros(S.np)])
+        out = S.solve(b, tol=1e-8, restart=30, max_iter=500)
+        assert out["status"] == 0
+        its.append(out["iters"])
+    assert its[1] <= its[0] + 4, its
+
+
 def test_adjoint_gradient_matches_central_differences(oracle_mod):
     """dL/dkappa_e = -lambda_e^T Khat_e u_e with A lambda = u - u_obs, against central
     differences of L = 0.5 ||u - u_obs||^2 computed with direct solves."""
