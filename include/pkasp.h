@@ -247,9 +247,44 @@ int pkasp_apply_vcycle(pkasp_problem *p, const double *b_dev, double *x_dev,
 
 /* Copies matrix `which` to host CSR arrays (any may be NULL); *nnz_out (may be NULL)
  * receives the entry count. which: 0 A_h, 1 A_H, 2 Pi, 3 + 2l AMG level l matrix A_l,
- * 4 + 2l the interpolation P_l of level l. Synchronises. ptr is [rows+1]. */
+ * 4 + 2l the interpolation P_l of level l; after pkasp_stokes_setup -1 B, -2 B^T,
+ * -3 M_p. Synchronises. ptr is [rows+1]. */
 int pkasp_get_matrix(const pkasp_problem *p, int which, int64_t *rows_out, int64_t *cols_out,
                      int64_t *nnz_out, int64_t *ptr_host, int32_t *col_host, double *val_host);
+
+/* ------------------------------------------------------------------------------------
+ * Stokes, Taylor-Hood P_k - P_{k-1} (Sec. 5), on the problem's mesh with k >= 2:
+ *   F = [A B^T; B 0], A = three copies of A_h (velocity unknowns component-major: entry
+ *   c n_h + j is component c of unknown j), B = -div_h with B_{q,(c,j)} = -int psi_q
+ *   d_c phi_j, pressure psi_q on every P_{k-1} node of the mesh (node numbering of the
+ *   DOF map of degree k-1 without Dirichlet removal; unknowns after the velocity, so a
+ *   vector has n = 3 n_h + n_p entries). The preconditioner is the block upper-triangular
+ *   Q_t = [A B^T; 0 -S]^{-1} of Eq. (5.4): z_p = -M_p^{-1} r_p by mp_iters steps of CG
+ *   with the diagonal of the pressure mass matrix M_p (from zero), then
+ *   z_u = B_aux (r_u - B^T z_p) with the problem's auxiliary-space preconditioner per
+ *   component. F is singular in the constant pressure; right-hand sides with b_p = 0 are
+ *   consistent and the pressure is determined up to a constant.
+ * ---------------------------------------------------------------------------------- */
+
+/* Assembles B, B^T and M_p (host, from the mesh; setup work) and allocates the solver.
+ * Needs pkasp_setup first (its preconditioner approximates A^{-1}); a later pkasp_setup
+ * discards the Stokes data (call this again). Errors: EINVAL (k < 2, mp_iters outside
+ * 1..1000), ESTATE, ENOMEM, ECUDA. Synchronises. */
+int pkasp_stokes_setup(pkasp_problem *p, int mp_iters, pkasp_stream_t stream);
+
+/* sizes_out[5] = { n_h, n_p, n = 3 n_h + n_p, nnz(B), nnz(M_p) }. */
+int pkasp_stokes_sizes(const pkasp_problem *p, int64_t *sizes_out);
+
+/* y = F x and z = Q_t r for device vectors of n entries (enqueued on stream). */
+int pkasp_stokes_apply(pkasp_problem *p, const double *x_dev, double *y_dev, pkasp_stream_t stream);
+int pkasp_stokes_apply_prec(pkasp_problem *p, const double *r_dev, double *z_dev, pkasp_stream_t stream);
+
+/* FGMRES(options.restart) with Q_t on F x = b (device vectors of n entries; x holds the
+ * initial guess), to ||b - F x|| <= tol ||b - F x0|| (options.tol, max_iter), one CUDA
+ * graph per solve when use_graph. Fills *st (may be NULL; one column) and synchronises.
+ * Returns OK or ENOTCONV (or EINVAL / ESTATE / ECUDA). */
+int pkasp_stokes_solve(pkasp_problem *p, const double *b_dev, double *x_dev, pkasp_stats *st,
+                       pkasp_stream_t stream);
 
 /* Colouring (colour per row) of A_h (level = -1) or of AMG level l; returns the count in
  * *ncolours (may be NULL). */

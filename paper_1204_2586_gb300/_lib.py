@@ -86,6 +86,11 @@ SIGNATURES = [
     ("pkasp_dofmap_host", C.c_int, [vp, i64, vp, i64, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp]),
     ("pkasp_reference_tensors", C.c_int, [C.c_int, vp]),
     ("pkasp_time_kernel", C.c_int, [vp, C.c_int, C.c_int, C.POINTER(C.c_float), vp]),
+    ("pkasp_stokes_setup", C.c_int, [vp, C.c_int, vp]),
+    ("pkasp_stokes_sizes", C.c_int, [vp, vp]),
+    ("pkasp_stokes_apply", C.c_int, [vp, vp, vp, vp]),
+    ("pkasp_stokes_apply_prec", C.c_int, [vp, vp, vp, vp]),
+    ("pkasp_stokes_solve", C.c_int, [vp, vp, vp, C.POINTER(pkasp_stats), vp]),
 ]
 
 

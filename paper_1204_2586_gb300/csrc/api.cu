@@ -333,6 +333,7 @@ int pkasp_destroy(pkasp_problem *p) {
     if (!p) return PKASP_OK;
     cudaDeviceSynchronize();
     pk::free_setup(p);
+    pk::stokes_free(p);
     p->stage_pool.free_all();
     p->pool.free_all();
     if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
@@ -384,7 +385,11 @@ int pkasp_get_matrix(const pkasp_problem *p, int which, int64_t *rows_out, int64
                      int64_t *ptr_host, int32_t *col_host, double *val_host) {
     if (!p) return set_error(PKASP_EINVAL, "NULL problem");
     const pk::DCSR *A = nullptr;
-    if (which == 0) A = &p->Ah;
+    if (which < 0) {
+        if (!p->st) return set_error(PKASP_ESTATE, "pkasp_stokes_setup first");
+        A = pk::stokes_matrix(p, which);
+        if (!A) return set_error(PKASP_EINVAL, "unknown matrix");
+    } else if (which == 0) A = &p->Ah;
     else if (which == 1) A = &p->AH;
     else if (which == 2) A = &p->Pi;
     else if (which >= 3) {
@@ -403,6 +408,49 @@ int pkasp_get_matrix(const pkasp_problem *p, int which, int64_t *rows_out, int64
         if (ptr_host) PK_CUDA(cudaMemcpy(ptr_host, A->ptr, sizeof(int64_t) * (A->n + 1), cudaMemcpyDeviceToHost));
         if (col_host && A->nnz) PK_CUDA(cudaMemcpy(col_host, A->col, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost));
         if (val_host && A->nnz) PK_CUDA(cudaMemcpy(val_host, A->val, sizeof(double) * A->nnz, cudaMemcpyDeviceToHost));
+        return PKASP_OK;
+    });
+}
+
+int pkasp_stokes_setup(pkasp_problem *p, int mp_iters, pkasp_stream_t stream) {
+    if (!p) return set_error(PKASP_EINVAL, "NULL problem");
+    return guarded([&]() -> int {
+        pk::stokes_setup(p, mp_iters, (cudaStream_t)stream);
+        return PKASP_OK;
+    });
+}
+
+int pkasp_stokes_sizes(const pkasp_problem *p, int64_t *sizes_out) {
+    if (!p || !sizes_out) return set_error(PKASP_EINVAL, "NULL argument");
+    if (!p->st) return set_error(PKASP_ESTATE, "pkasp_stokes_setup first");
+    pk::stokes_sizes(p, sizes_out);
+    return PKASP_OK;
+}
+
+int pkasp_stokes_apply(pkasp_problem *p, const double *x_dev, double *y_dev, pkasp_stream_t stream) {
+    if (!p || !x_dev || !y_dev) return set_error(PKASP_EINVAL, "NULL argument");
+    return guarded([&]() -> int {
+        pk::stokes_apply(p, x_dev, y_dev, (cudaStream_t)stream);
+        return PKASP_OK;
+    });
+}
+
+int pkasp_stokes_apply_prec(pkasp_problem *p, const double *r_dev, double *z_dev, pkasp_stream_t stream) {
+    if (!p || !r_dev || !z_dev) return set_error(PKASP_EINVAL, "NULL argument");
+    return guarded([&]() -> int {
+        pk::stokes_prec(p, r_dev, z_dev, (cudaStream_t)stream);
+        if (p->fine_tpr < -1) pk::check_barrier(p, (cudaStream_t)stream);
+        return PKASP_OK;
+    });
+}
+
+int pkasp_stokes_solve(pkasp_problem *p, const double *b_dev, double *x_dev, pkasp_stats *st,
+                       pkasp_stream_t stream) {
+    if (!p || !b_dev || !x_dev) return set_error(PKASP_EINVAL, "NULL argument");
+    if (!p->st) return set_error(PKASP_ESTATE, "pkasp_stokes_setup first");
+    return guarded([&]() -> int {
+        const int rc = pk::stokes_solve(p, b_dev, x_dev, st, (cudaStream_t)stream);
+        if (rc != PKASP_OK) return set_error(rc, "FGMRES on the Stokes system reached max_iter before the tolerance");
         return PKASP_OK;
     });
 }

@@ -106,7 +106,8 @@ struct Level {
     float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr;
 };
 
-struct GmresState;  // gmres.cu
+struct GmresState;  // gmres.cuh
+struct StokesWork;  // stokes.cu
 
 // Scalars of one PCG run (device), per column.
 struct PcgState {
@@ -228,6 +229,8 @@ struct pkasp_problem {
     const void *gm_key_b = nullptr;
     void *gm_key_x = nullptr;
     long long gm_g_init = 0, gm_g_body = 0;
+    // Taylor-Hood Stokes system (stokes.cpp, stokes.cu), built by pkasp_stokes_setup
+    pk::StokesWork *st = nullptr;
     // staging of host arrays [n][ld]
     pk::DevPool stage_pool;
     int64_t stage_elems = 0;
@@ -248,6 +251,7 @@ struct DofMap {
     std::vector<int64_t> dof_all;
     std::vector<double> dof_xyz;
     std::vector<int32_t> elem_dof, elem_vdof;
+    std::vector<int32_t> elem_all;  // [nt*nloc] node index before Dirichlet removal
     std::vector<int64_t> inc_ptr, vinc_ptr;
     std::vector<int32_t> inc, vinc;  // tet*64 + local index
     HCSR Ah_pattern, AH_pattern, Pi, PiT;
@@ -286,6 +290,16 @@ float time_batched(pkasp_problem *p, int which, int reps, cudaStream_t s);
 // FGMRES(m) outer iteration (gmres.cu); b and x device vectors [n_h]
 int solve_gmres(pkasp_problem *p, const double *b, double *x, pkasp_stats *st, cudaStream_t s);
 void free_gmres(pkasp_problem *p);
+// Stokes (stokes.cpp: host assembly of B = -div_h, B^T and the pressure mass matrix;
+// stokes.cu: operator, block preconditioner, FGMRES)
+void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t &np);
+void stokes_setup(pkasp_problem *p, int mp_iters, cudaStream_t s);
+void stokes_free(pkasp_problem *p);
+void stokes_apply(pkasp_problem *p, const double *x, double *y, cudaStream_t s);
+void stokes_prec(pkasp_problem *p, const double *r, double *z, cudaStream_t s);
+int stokes_solve(pkasp_problem *p, const double *b, double *x, pkasp_stats *st, cudaStream_t s);
+const DCSR *stokes_matrix(const pkasp_problem *p, int which);  // -1 B, -2 B^T, -3 M_p
+void stokes_sizes(const pkasp_problem *p, int64_t *out5);
 float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s);
 
 // SELL-32 builders (sell.cu)

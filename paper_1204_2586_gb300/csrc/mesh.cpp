@@ -386,6 +386,9 @@ void build_dofmap(const HostMesh &M, DofMap &D) {
         if (cmap[d] >= 0) D.dof_all[cmap[d]] = d;
     D.elem_dof.resize((size_t)nt * nl);
     for (size_t i = 0; i < elem_all.size(); ++i) D.elem_dof[i] = (int32_t)cmap[elem_all[i]];
+    if (D.n_all > INT32_MAX) fail(PKASP_EINVAL, "more than 2^31 nodes");
+    D.elem_all.resize(elem_all.size());
+    for (size_t i = 0; i < elem_all.size(); ++i) D.elem_all[i] = (int32_t)elem_all[i];
     std::vector<int64_t> vmap(nv);
     int64_t nH = 0;
     for (int64_t v = 0; v < nv; ++v) vmap[v] = vb[v] ? -1 : nH++;

@@ -611,6 +611,7 @@ __global__ void __launch_bounds__(kBlock) k_true_residual(int64_t n, RowOp A, co
 void free_setup(pkasp_problem *p) {
     free_batched(p);
     free_gmres(p);
+    stokes_free(p);  // its solver captured the preconditioner being replaced
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     p->graph_exec = nullptr;

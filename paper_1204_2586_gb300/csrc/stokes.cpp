@@ -1,0 +1,228 @@
+// stokes.cpp -- host assembly of the Taylor-Hood P_k - P_{k-1} Stokes blocks (Sec. 5):
+// B = -div_h (rows: the P_{k-1} pressure nodes, all of them; columns: the velocity
+// unknowns, component-major c n_h + j), its transpose and the pressure mass matrix M_p.
+// One-off setup work, like the DOF map: the element integrals come from reference
+// tensors computed once by Grundmann-Moeller quadrature, and every row sums its
+// elements in ascending element order (rows in parallel).
+#include <algorithm>
+#include <cmath>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace pk {
+
+namespace {
+
+template <class F>
+void rows_parallel(int64_t n, F fn) {
+    unsigned hw = std::thread::hardware_concurrency();
+    int nth = (int)std::max(1u, std::min(hw ? hw : 1u, 32u));
+    if (n < 2048) nth = 1;
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + nth - 1) / nth;
+    for (int t = 0; t < nth; ++t) {
+        const int64_t b = t * chunk, e = std::min(n, b + chunk);
+        if (b >= e) break;
+        if (nth == 1) {
+            fn(b, e);
+            return;
+        }
+        th.emplace_back([=] { fn(b, e); });
+    }
+    for (auto &x : th) x.join();
+}
+
+// value and derivative in t of prod_{i<j} (k t - i) / (i + 1)
+void lag_1d(int k, int j, double t, double &v, double &dv) {
+    v = 1.0;
+    dv = 0.0;
+    for (int i = 0; i < j; ++i) {
+        const double f = ((double)k * t - (double)i) / (double)(i + 1);
+        dv = dv * f + v * (double)k / (double)(i + 1);
+        v *= f;
+    }
+}
+
+// grad lambda_a (rows) of a tetrahedron and its volume
+double tet_gradients(const double *X, double g[4][3]) {
+    double J[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) J[r][c] = X[3 * (c + 1) + r] - X[r];
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    // rows of J^{-1} = gradients of lambda_1..3
+    const double inv[3][3] = {{c00 / det, (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det,
+                               (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det},
+                              {c01 / det, (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det,
+                               (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det},
+                              {c02 / det, (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det,
+                               (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det}};
+    for (int c = 0; c < 3; ++c) {
+        g[1][c] = inv[0][c];
+        g[2][c] = inv[1][c];
+        g[3][c] = inv[2][c];
+        g[0][c] = -(inv[0][c] + inv[1][c] + inv[2][c]);
+    }
+    return det / 6.0;
+}
+
+// incidence node -> (element, local) with elements ascending
+void node_incidence(int64_t nnodes, int64_t nt, int nl, const std::vector<int32_t> &emap,
+                    std::vector<int64_t> &ptr, std::vector<int64_t> &ent) {
+    ptr.assign(nnodes + 1, 0);
+    for (int64_t t = 0; t < nt; ++t)
+        for (int m = 0; m < nl; ++m) {
+            const int32_t q = emap[t * nl + m];
+            if (q >= 0) ptr[q + 1]++;
+        }
+    for (int64_t i = 0; i < nnodes; ++i) ptr[i + 1] += ptr[i];
+    ent.assign(ptr[nnodes], 0);
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t t = 0; t < nt; ++t)
+        for (int m = 0; m < nl; ++m) {
+            const int32_t q = emap[t * nl + m];
+            if (q >= 0) ent[fill[q]++] = t * 64 + m;
+        }
+}
+
+}  // namespace
+
+void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t &np) {
+    const int k = p->k, kp = k - 1;
+    const int nu = nloc_of(k), npl = nloc_of(kp);
+    const int64_t nt = p->nt, nh = p->nh;
+    HostMesh hm{kp, p->nv, nt, p->xyz.data(), p->tets.data()};
+    DofMap Dp;
+    build_dofmap(hm, Dp);
+    np = Dp.n_all;
+    // reference tensors by quadrature: R[a][m][n] = (1/|T|) int psi_m dphi_n/dlambda_a,
+    // Mr[m][q] = (1/|T|) int psi_m psi_q (the rule is exact to degree 2(k-1)+1)
+    std::vector<double> lam, w;
+    gm_rule(std::max(kp, 1), lam, w);
+    const int nq = (int)w.size();
+    std::vector<int> mu, mp;
+    ref_nodes(k, mu);
+    ref_nodes(kp, mp);
+    std::vector<double> R((size_t)4 * npl * nu, 0.0), Mr((size_t)npl * npl, 0.0);
+    std::vector<double> psi(npl), dphi((size_t)4 * nu);
+    for (int q = 0; q < nq; ++q) {
+        const double *l = &lam[4 * q];
+        basis_values(kp, l, psi.data());
+        for (int n = 0; n < nu; ++n) {
+            double v[4], d[4];
+            for (int a = 0; a < 4; ++a) lag_1d(k, mu[4 * n + a], l[a], v[a], d[a]);
+            for (int a = 0; a < 4; ++a) {
+                double prod = d[a];
+                for (int b = 0; b < 4; ++b)
+                    if (b != a) prod *= v[b];
+                dphi[a * nu + n] = prod;
+            }
+        }
+        for (int a = 0; a < 4; ++a)
+            for (int m = 0; m < npl; ++m)
+                for (int n = 0; n < nu; ++n) R[((size_t)a * npl + m) * nu + n] += 6.0 * w[q] * psi[m] * dphi[a * nu + n];
+        for (int m = 0; m < npl; ++m)
+            for (int r = 0; r < npl; ++r) Mr[(size_t)m * npl + r] += 6.0 * w[q] * psi[m] * psi[r];
+    }
+    // element geometry
+    std::vector<double> grads((size_t)nt * 12), vols(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        double X[12], g[4][3];
+        for (int v = 0; v < 4; ++v)
+            for (int c = 0; c < 3; ++c) X[3 * v + c] = p->xyz[3 * (int64_t)p->tets[4 * t + v] + c];
+        vols[t] = tet_gradients(X, g);
+        for (int a = 0; a < 4; ++a)
+            for (int c = 0; c < 3; ++c) grads[t * 12 + a * 3 + c] = g[a][c];
+    }
+    std::vector<int64_t> iptr, ient;
+    node_incidence(np, nt, npl, Dp.elem_all, iptr, ient);
+    // pattern per pressure row: sorted unique columns
+    B.n = np;
+    B.m = 3 * nh;
+    M.n = np;
+    M.m = np;
+    B.ptr.assign(np + 1, 0);
+    M.ptr.assign(np + 1, 0);
+    std::vector<std::vector<int32_t>> bcols(np), mcols(np);
+    rows_parallel(np, [&](int64_t b, int64_t e) {
+        std::vector<int32_t> bc, mc;
+        for (int64_t q = b; q < e; ++q) {
+            bc.clear();
+            mc.clear();
+            for (int64_t x = iptr[q]; x < iptr[q + 1]; ++x) {
+                const int64_t t = ient[x] / 64;
+                for (int n = 0; n < nu; ++n) {
+                    const int32_t j = p->elem_dof[t * nu + n];
+                    if (j < 0) continue;
+                    for (int c = 0; c < 3; ++c) bc.push_back((int32_t)(c * nh + j));
+                }
+                for (int r = 0; r < npl; ++r) mc.push_back(Dp.elem_all[t * npl + r]);
+            }
+            std::sort(bc.begin(), bc.end());
+            bc.erase(std::unique(bc.begin(), bc.end()), bc.end());
+            std::sort(mc.begin(), mc.end());
+            mc.erase(std::unique(mc.begin(), mc.end()), mc.end());
+            bcols[q] = bc;
+            mcols[q] = mc;
+        }
+    });
+    for (int64_t q = 0; q < np; ++q) {
+        B.ptr[q + 1] = B.ptr[q] + (int64_t)bcols[q].size();
+        M.ptr[q + 1] = M.ptr[q] + (int64_t)mcols[q].size();
+    }
+    B.col.resize(B.ptr[np]);
+    B.val.assign(B.ptr[np], 0.0);
+    M.col.resize(M.ptr[np]);
+    M.val.assign(M.ptr[np], 0.0);
+    rows_parallel(np, [&](int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; ++q) {
+            std::copy(bcols[q].begin(), bcols[q].end(), B.col.begin() + B.ptr[q]);
+            std::copy(mcols[q].begin(), mcols[q].end(), M.col.begin() + M.ptr[q]);
+            const int32_t *bcb = &B.col[B.ptr[q]], *bce = bcb + bcols[q].size();
+            const int32_t *mcb = &M.col[M.ptr[q]], *mce = mcb + mcols[q].size();
+            for (int64_t x = iptr[q]; x < iptr[q + 1]; ++x) {
+                const int64_t t = ient[x] / 64;
+                const int m = (int)(ient[x] % 64);
+                const double vol = vols[t];
+                const double *g = &grads[t * 12];
+                for (int n = 0; n < nu; ++n) {
+                    const int32_t j = p->elem_dof[t * nu + n];
+                    if (j < 0) continue;
+                    for (int c = 0; c < 3; ++c) {
+                        double s = 0.0;
+                        for (int a = 0; a < 4; ++a) s += g[a * 3 + c] * R[((size_t)a * npl + m) * nu + n];
+                        const int32_t col = (int32_t)(c * nh + j);
+                        const int64_t pos = std::lower_bound(bcb, bce, col) - bcb;
+                        B.val[B.ptr[q] + pos] += -vol * s;
+                    }
+                }
+                for (int r = 0; r < npl; ++r) {
+                    const int32_t col = Dp.elem_all[t * npl + r];
+                    const int64_t pos = std::lower_bound(mcb, mce, col) - mcb;
+                    M.val[M.ptr[q] + pos] += vol * Mr[(size_t)m * npl + r];
+                }
+            }
+        }
+    });
+    // B^T: columns of B become rows, entries in ascending pressure row
+    BT.n = 3 * nh;
+    BT.m = np;
+    BT.ptr.assign(BT.n + 1, 0);
+    for (int64_t x = 0; x < B.ptr[np]; ++x) BT.ptr[B.col[x] + 1]++;
+    for (int64_t i = 0; i < BT.n; ++i) BT.ptr[i + 1] += BT.ptr[i];
+    BT.col.resize(B.ptr[np]);
+    BT.val.resize(B.ptr[np]);
+    std::vector<int64_t> fill(BT.ptr.begin(), BT.ptr.end() - 1);
+    for (int64_t q = 0; q < np; ++q)
+        for (int64_t x = B.ptr[q]; x < B.ptr[q + 1]; ++x) {
+            const int64_t o = fill[B.col[x]]++;
+            BT.col[o] = (int32_t)q;
+            BT.val[o] = B.val[x];
+        }
+}
+
+}  // namespace pk

@@ -177,6 +177,50 @@ class Problem:
         return lam, dict(iters=list(st.iters[:ncols]), status=list(st.status[:ncols]),
                          true_rel=list(st.true_rel[:ncols]))
 
+    # ---- Stokes (Taylor-Hood P_k - P_{k-1}) ---------------------------------------
+    def stokes_setup(self, mp_iters=10, stream=None):
+        """B = -div_h, B^T, M_p and the block preconditioner; needs setup() first."""
+        L.check(L.load().pkasp_stokes_setup(self.h, int(mp_iters), _stream(stream)))
+        sz = np.zeros(5, np.int64)
+        L.check(L.load().pkasp_stokes_sizes(self.h, sz.ctypes.data))
+        self.stokes_nh, self.stokes_np, self.stokes_n = int(sz[0]), int(sz[1]), int(sz[2])
+        return self
+
+    def stokes_apply(self, x, stream=None):
+        import torch
+
+        y = torch.empty_like(x)
+        L.check(L.load().pkasp_stokes_apply(self.h, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def stokes_prec(self, r, stream=None):
+        import torch
+
+        z = torch.empty_like(r)
+        L.check(L.load().pkasp_stokes_apply_prec(self.h, _ptr(r), _ptr(z), _stream(stream)))
+        return z
+
+    def stokes_solve(self, b, x=None, hist_cap=0, stream=None, raise_on_fail=True):
+        """FGMRES with Q_t on F x = b (CUDA tensors of n = 3 n_h + n_p entries)."""
+        import torch
+
+        if x is None:
+            x = torch.zeros_like(b)
+        st = L.pkasp_stats()
+        hist = None
+        if hist_cap > 0:
+            hist = np.zeros(hist_cap)
+            st.hist_host = hist.ctypes.data_as(C.POINTER(C.c_double))
+            st.hist_cap = hist_cap
+        rc = L.load().pkasp_stokes_solve(self.h, _ptr(b), _ptr(x), C.byref(st), _stream(stream))
+        if rc not in (L.PKASP_OK, L.PKASP_ENOTCONV) or (rc != L.PKASP_OK and raise_on_fail):
+            L.check(rc)
+        out = dict(rc=rc, iters=st.iters[0], status=st.status[0], true_rel=st.true_rel[0],
+                   restarts=st.restarts, solve_ms=st.solve_ms, kernel_launches=int(st.kernel_launches))
+        if hist is not None:
+            out["hist"] = hist[: st.hist_len].copy()
+        return x, out
+
     def spmv(self, x, stream=None):
         import torch
 
