@@ -236,7 +236,8 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD["name"],
-                    choices=[WORKLOAD["name"], P4["name"], BATCHED["name"], "theta_study", "cop_study"])
+                    choices=[WORKLOAD["name"], P4["name"], BATCHED["name"], "theta_study", "cop_study",
+                             "stokes_study"])
     ap.add_argument("--smoother-layout", type=int, default=0,
                     help="pin the fine smoother layout (pkasp_options.smoother_layout) instead of "
                          "autotuning it; for profiler runs, under which the autotuner's timings "
@@ -274,6 +275,9 @@ def main():
         return
     if args.workload == "cop_study":
         run_cop_study(args)
+        return
+    if args.workload == "stokes_study":
+        run_stokes_study(args)
         return
     if args.workload == BATCHED["name"]:
         run_batched(args, ws, rank, local)
@@ -521,6 +525,46 @@ def run_cop_study(args):
                       "paper_table6": {"P2": {"AMG": 1.67, "P1-AMG": 1.76, "GAMG": 1.12},
                                        "P3": {"AMG": 1.56, "P1-AMG": 1.96, "GAMG": 1.02},
                                        "P4": {"AMG": 1.36, "P1-AMG": 1.70, "GAMG": 1.01}}}))
+
+
+STOKES_STUDY = [(2, 12), (2, 24), (3, 8), (3, 16), (4, 6), (4, 12)]  # (k, cubes per side)
+
+
+def run_stokes_study(args):
+    """Taylor-Hood P_k - P_{k-1} Stokes (Sec. 5, Sec. 6.3): FGMRES(30) with the block
+    upper-triangular preconditioner Q_t (one auxiliary-space cycle per velocity component,
+    10 diagonal-PCG steps on the pressure mass matrix), theta = 0.8 as in Sec. 6.3, to
+    relative residual 1e-8; two mesh sizes per k show whether the step count grows with
+    the number of unknowns. The right-hand side has i.i.d. N(0,1) velocity entries
+    (seed 2) and a zero pressure part. One JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_1204_2586_gb300 import Problem
+    from paper_1204_2586_gb300.inputs import kuhn_mesh, rhs_normal
+
+    rows = []
+    for k, n in STOKES_STUDY:
+        xyz, t = kuhn_mesh(n, 0.2, 0)
+        G = Problem(xyz, t, k)
+        G.setup(theta=0.8, level_smoother=LEVEL_SMOOTHER, max_iter=1000)
+        t0 = time.perf_counter()
+        G.stokes_setup(10)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        nu = 3 * G.stokes_nh
+        b = torch.tensor(np.concatenate([rhs_normal(nu, 1, 2)[:, 0], np.zeros(G.stokes_np)]), device="cuda")
+        x = torch.zeros_like(b)
+        G.stokes_solve(b, x)
+        x.zero_()
+        _, st = G.stokes_solve(b, x)
+        rows.append({"k": k, "n": n, "velocity_unknowns": nu, "pressure_unknowns": G.stokes_np,
+                     "unknowns": G.stokes_n, "iterations": st["iters"], "restarts": st["restarts"],
+                     "status": st["status"], "true_rel_residual": st["true_rel"],
+                     "solve_s": st["solve_ms"] / 1e3, "stokes_setup_s": setup_s})
+        G.close()
+    print(json.dumps({"study": "stokes_taylor_hood", "krylov": "FGMRES(30)", "preconditioner": "Q_t",
+                      "theta": 0.8, "tol": 1e-8, "rows": rows}))
 
 
 def run_batched(args, ws, rank, local):
