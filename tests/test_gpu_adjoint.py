@@ -3,7 +3,7 @@ against central differences of the loss (step 1e-6, forward solves to 1e-13)."""
 import numpy as np
 import pytest
 
-from paper_1204_2586_gb300.inputs import kappa_lognormal, kuhn_mesh, uniform01
+from paper_1204_2586_gb300.inputs import kappa_lognormal, kuhn_mesh, rhs_normal, uniform01
 
 pytestmark = pytest.mark.gpu
 
@@ -89,3 +89,33 @@ def test_adjoint_gradient_central_differences_p3_n24(torch_cuda):
     err6 = _fd_check(torch_cuda, 24, 3, 16, 2e-3, eps=1e-6)
     err4 = _fd_check(torch_cuda, 24, 3, 16, 1e-5, eps=1e-4)
     print(f"max relative FD error over 16 elements: step 1e-6 {err6:.2e}, step 1e-4 {err4:.2e}")
+
+
+def test_adjoint_block_of_right_hand_sides(torch_cuda):
+    """[n_h, 2] right-hand sides through one differentiable block solve: dL/dkappa is the
+    sum of the two single-column gradients, dL/db the block of adjoint solutions."""
+    torch = torch_cuda
+    from paper_1204_2586_gb300 import Problem
+    from paper_1204_2586_gb300.autograd import solve
+
+    xyz, t = kuhn_mesh(4, 0.2, 0)
+    nt = t.shape[0]
+    P = Problem(xyz, t, 2, kappa_lognormal(nt, 1))
+    skw = dict(tol=1e-13, max_iter=1000)
+    B = torch.tensor(np.ascontiguousarray(rhs_normal(P.nh, 2, 5)), device="cuda")
+    W = torch.tensor(np.ascontiguousarray(rhs_normal(P.nh, 2, 6)), device="cuda")
+
+    def grads(b, w):
+        kap = torch.tensor(kappa_lognormal(nt, 1), dtype=torch.float64, requires_grad=True)
+        bb = b.clone().requires_grad_(True)
+        u = solve(kap, bb, P, **skw)
+        (w * u).sum().backward()
+        return kap.grad.cpu().numpy(), bb.grad.cpu().numpy()
+
+    gk, gb = grads(B, W)
+    parts = [grads(B[:, c].contiguous(), W[:, c].contiguous()) for c in range(2)]
+    gk_sum = parts[0][0] + parts[1][0]
+    assert np.abs(gk - gk_sum).max() <= 1e-9 * np.abs(gk_sum).max()
+    for c in range(2):
+        assert np.abs(gb[:, c] - parts[c][1]).max() <= 1e-9 * np.abs(parts[c][1]).max()
+    P.close()
