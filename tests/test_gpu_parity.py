@@ -214,7 +214,7 @@ def test_fp32_preconditioner(pair, torch_cuda):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("lanes", [4, 8])
+@pytest.mark.parametrize("lanes", [4, 8, 16])
 def test_persistent_smoother_matches_phase_launches(pair, torch_cuda, prec, lanes):
     """The whole symmetric sweep in one cooperative launch (grid barriers between colours),
     and the phases with two rows per lane group, add the same products in the same order
