@@ -415,6 +415,8 @@ def main():
                                  "CSR, lanes per colour" if info64.smoother_layout == -1 else
                                  f"one cooperative launch, CSR x{-info64.smoother_layout} lanes"
                                  if info64.smoother_layout < -1 else
+                                 f"CSR x{info64.smoother_layout % 100} lanes, grid-stride over the "
+                                 "resident blocks" if info64.smoother_layout > 400 else
                                  f"CSR x{info64.smoother_layout - 100} lanes, two rows per lane group"
                                  if info64.smoother_layout > 100 else
                                  f"CSR x{info64.smoother_layout} lanes"),

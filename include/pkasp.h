@@ -85,7 +85,11 @@ typedef struct {
                              2 = per phase, SELL-32; 3 = per phase, CSR with 2 lanes per
                              row; 4, 8, 16 = per phase, CSR with that many lanes per row;
                              102, 104, 108, 116 = per phase, CSR with 2, 4, 8, 16 lanes and
-                             two rows per lane group; -4, -8, -16 = the whole
+                             two rows per lane group; 404, 408, 416 = per phase, CSR
+                             with 4, 8, 16 lanes per row over a grid of the kernel's
+                             resident blocks, each lane group striding over rows and
+                             loading the next row's entries during the current row's
+                             gathers; -4, -8, -16 = the whole
                              symmetric sweep in one cooperative launch with that many
                              lanes per row.
                              spmv_threads != 0 overrides it with its own lane count. */
@@ -122,7 +126,8 @@ typedef struct {
                                per row), t > 0 = CSR read by t lanes per row */
     int smoother_layout;    /* same for the fine smoother's colour phases; -1 = CSR with
                                lanes fitted per colour; 100 + t = t lanes, two rows per
-                               lane group; -t (t > 1) = the whole symmetric sweep in one
+                               lane group; 400 + t = t lanes, grid-stride over the resident
+                               blocks; -t (t > 1) = the whole symmetric sweep in one
                                cooperative launch, t lanes per row */
     int block_width;        /* columns of the internal multi-RHS blocks (4, 8, 16, 32, 48
                                or 64) of the last solve with ncols > 1; 0 before one */

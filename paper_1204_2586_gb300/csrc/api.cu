@@ -256,9 +256,10 @@ int pkasp_setup(pkasp_problem *p, const pkasp_options *opt, pkasp_stream_t strea
     {
         const int l = o.smoother_layout;
         if (!(l == 0 || l == 1 || l == 2 || l == 3 || l == 4 || l == 8 || l == 16 || l == -4 || l == -8 ||
-              l == -16 || l == 102 || l == 104 || l == 108 || l == 116))
-            return set_error(PKASP_EINVAL,
-                             "smoother_layout must be 0, 1, 2, 3, 4, 8, 16, -4, -8, -16, 102, 104, 108 or 116");
+              l == -16 || l == 102 || l == 104 || l == 108 || l == 116 || l == 404 || l == 408 ||
+              l == 416))
+            return set_error(PKASP_EINVAL, "smoother_layout must be 0, 1, 2, 3, 4, 8, 16, -4, -8, -16, 102, 104, "
+                                           "108, 116, 404, 408 or 416");
     }
     return guarded([&]() -> int {
         auto t0 = std::chrono::steady_clock::now();

@@ -235,6 +235,105 @@ __global__ void __launch_bounds__(kBlock) k_gs_phase(int64_t pb, int64_t pe, con
     if (lead) y[i] = BACK ? own - acc * di : (own - acc) * di;
 }
 
+// The same phase over a capped grid: sub-warp g takes rows pb + g, pb + g + nsub, ...
+// (nsub sub-warps in the grid) and loads the next row's position, diagonal and first
+// batch of entries while the current row's gathers are in flight, with the bounds of
+// the row after that one step further ahead. Each row's sum is formed exactly as in
+// k_gs_phase<TPR, NB> (bitwise the same result). The grid is at most the blocks that
+// are resident at once, so on phases of several waves no block waits for a slot and
+// every lane group keeps a row's loads in flight behind the current one.
+// The loop runs while the warp's first sub-warp has a row, so every lane of the warp
+// reaches the shuffles; a sub-warp past the end takes no entries and stores nothing.
+template <int TPR, int NB, typename PT>
+__device__ __forceinline__ void gs_row_static(int64_t q, bool ok, bool lead, int sub, int64_t lo, int64_t hi,
+                                              const int32_t *__restrict__ perm, const int32_t *__restrict__ xcol,
+                                              const PT *__restrict__ xval, const PT *__restrict__ dinv,
+                                              int32_t &i, PT &di, int (&c)[NB], PT (&v)[NB]) {
+    i = (ok && lead) ? perm[q] : 0;
+    di = (ok && lead) ? dinv[q] : PT(1);
+    const int64_t b0 = lo + sub;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        const int64_t e = b0 + (int64_t)k * TPR;
+        const bool in = e < hi;
+        c[k] = in ? __ldg(&xcol[e]) : -1;
+        v[k] = in ? __ldg(&xval[e]) : PT(0);
+    }
+}
+
+template <int TPR, int NB, typename PT, typename TR, bool BACK>
+__global__ void __launch_bounds__(kBlock) k_gs_phase_gs(int64_t pb, int64_t pe, const int32_t *__restrict__ perm,
+                                                        const int64_t *__restrict__ xptr,
+                                                        const int32_t *__restrict__ xcol,
+                                                        const PT *__restrict__ xval, const PT *__restrict__ dinv,
+                                                        const TR *r, PT *y) {
+    pdl_trigger();
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nsub = (int64_t)gridDim.x * blockDim.x / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool lead = sub == 0;
+    int64_t p = pb + gt / TPR;
+    int64_t pw = pb + (gt & ~(int64_t)31) / TPR;  // the warp's first sub-warp's row
+    bool ok = p < pe;
+    int64_t lo = ok ? xptr[p] : 0, hi = ok ? xptr[p + 1] : 0;
+    int32_t i;
+    PT di;
+    int c[NB];
+    PT v[NB];
+    gs_row_static<TPR, NB, PT>(p, ok, lead, sub, lo, hi, perm, xcol, xval, dinv, i, di, c, v);
+    int64_t pn = p + nsub;
+    int64_t lon = pn < pe ? xptr[pn] : 0, hin = pn < pe ? xptr[pn + 1] : 0;
+    pdl_wait();
+    while (pw < pe) {
+        // next row: static loads now, consumed in the next pass
+        const bool okn = pn < pe;
+        int32_t i_n;
+        PT di_n;
+        int cn[NB];
+        PT vn[NB];
+        gs_row_static<TPR, NB, PT>(pn, okn, lead, sub, lon, hin, perm, xcol, xval, dinv, i_n, di_n, cn, vn);
+        const int64_t pnn = pn + nsub;
+        const int64_t lonn = pnn < pe ? xptr[pnn] : 0, hinn = pnn < pe ? xptr[pnn + 1] : 0;
+        // this row
+        PT own = PT(0);
+        if (ok && lead) own = BACK ? y[i] : (PT)r[i];
+        PT acc = PT(0);
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            if (c[k] >= 0) acc += v[k] * y[c[k]];
+        for (int64_t base = lo + sub + (int64_t)NB * TPR; base < hi; base += (int64_t)NB * TPR) {
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int64_t e = base + (int64_t)k * TPR;
+                const bool in = e < hi;
+                c[k] = in ? __ldg(&xcol[e]) : -1;
+                v[k] = in ? __ldg(&xval[e]) : PT(0);
+            }
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                if (c[k] >= 0) acc += v[k] * y[c[k]];
+        }
+        acc = subwarp_sum<TPR>(acc);
+        if (ok && lead) y[i] = BACK ? own - acc * di : (own - acc) * di;
+        // advance
+        p = pn;
+        pw += nsub;
+        ok = okn;
+        i = i_n;
+        di = di_n;
+        lo = lon;
+        hi = hin;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            c[k] = cn[k];
+            v[k] = vn[k];
+        }
+        pn = pnn;
+        lon = lonn;
+        hin = hinn;
+    }
+}
+
 // The same phase with two rows per sub-warp: rows p and p + half of the colour (no edge
 // joins two rows of one colour, so neither reads the other's result). Both rows' loads
 // are issued before either row's gathers, doubling the loads in flight per lane for

@@ -133,6 +133,34 @@ int batch_for(int tpr, int len) {
         default: { constexpr int NB = 8; BODY; } break;  \
     }
 
+// Grid-stride colour phases (k_gs_phase_gs): at most the kernel's resident blocks (a
+// grid of half of them lost on every measured problem). The capacity is taken once per
+// kernel variant.
+template <auto Kern>
+unsigned phase_grid(int64_t rows, int tpr) {
+    static int occ = 0, nsm = 0;
+    if (occ == 0) {
+        int dev = 0, o = 0;
+        PK_CUDA(cudaGetDevice(&dev));
+        PK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        PK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, Kern, kBlock, 0));
+        occ = std::max(1, o);
+    }
+    return (unsigned)std::min<int64_t>(rows_grid(rows, tpr), (int64_t)nsm * occ);
+}
+#define PK_TPR3_SWITCH(tpr, BODY)                         \
+    switch (tpr) {                                        \
+        case 4: { constexpr int TPR = 4; BODY; } break;   \
+        case 16: { constexpr int TPR = 16; BODY; } break; \
+        default: { constexpr int TPR = 8; BODY; } break;  \
+    }
+#define PK_NB3_SWITCH(nb, BODY)                          \
+    switch (nb) {                                        \
+        case 2: { constexpr int NB = 2; BODY; } break;   \
+        case 4: { constexpr int NB = 4; BODY; } break;   \
+        default: { constexpr int NB = 8; BODY; } break;  \
+    }
+
 // colour phases of a forward sweep from zero: y = (D+L)^{-1} r; tpr < 0 picks the lanes
 // per colour from the colour's longest lower part
 template <typename PT, typename TR>
@@ -140,6 +168,16 @@ void gs_forward0(const DSplit &sp, int tpr_fixed, const TR *r, PT *y, cudaStream
     for (int c = 0; c < sp.ncol; ++c) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
+        if (tpr_fixed > 400) {  // grid-stride with prefetch of the next row
+            const int tpr = tpr_fixed % 100;
+            const int nb = batch_for(tpr, sp.l90[c]);
+            PK_TPR3_SWITCH(tpr, PK_NB3_SWITCH(nb, (launch_pdl(
+                k_gs_phase_gs<TPR, NB, PT, TR, false>,
+                phase_grid<k_gs_phase_gs<TPR, NB, PT, TR, false>>(pe - pb, TPR), s, pb, pe,
+                (const int32_t *)sp.perm, (const int64_t *)sp.lptr, (const int32_t *)sp.lcol,
+                pick<PT>(sp.lval, sp.lval32), pick<PT>(sp.dinv, sp.dinv32), r, y))));
+            continue;
+        }
         const bool two = tpr_fixed > 100;  // two rows per sub-warp
         const int tf = two ? tpr_fixed - 100 : tpr_fixed;
         const int tpr = tf > 0 ? tf : lanes_for(sp.lmax[c]);
@@ -167,6 +205,16 @@ void gs_backward0(const DSplit &sp, int tpr_fixed, PT *y, cudaStream_t s) {
     for (int c = sp.ncol - 2; c >= 0; --c) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
+        if (tpr_fixed > 400) {
+            const int tpr = tpr_fixed % 100;
+            const int nb = batch_for(tpr, sp.u90[c]);
+            PK_TPR3_SWITCH(tpr, PK_NB3_SWITCH(nb, (launch_pdl(
+                k_gs_phase_gs<TPR, NB, PT, PT, true>,
+                phase_grid<k_gs_phase_gs<TPR, NB, PT, PT, true>>(pe - pb, TPR), s, pb, pe,
+                (const int32_t *)sp.perm, (const int64_t *)sp.uptr, (const int32_t *)sp.ucol,
+                pick<PT>(sp.uval, sp.uval32), pick<PT>(sp.dinv, sp.dinv32), (const PT *)y, y))));
+            continue;
+        }
         const bool two = tpr_fixed > 100;
         const int tf = two ? tpr_fixed - 100 : tpr_fixed;
         const int tpr = tf > 0 ? tf : lanes_for(sp.umax[c]);
@@ -386,8 +434,10 @@ void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s) 
     // multiplicative: forward GS (or l1 step) from zero, coarse correction of the new
     // residual, backward GS sweep (or l1 step) from the corrected iterate
     const bool jac = p->opt.smoother == PKASP_SMOOTHER_L1JACOBI;
-    // the full backward sweep uses the CSR split (one row per lane group)
-    const int ts = p->fine_tpr > 100 ? p->fine_tpr - 100 : p->fine_tpr > 0 ? p->fine_tpr : -1;
+    // the forward half sweep takes the tuned layout (SELL-32 maps to lanes fitted per
+    // colour); the full backward sweep uses the CSR split with one row per lane group
+    const int tfw = p->fine_tpr > 0 ? p->fine_tpr : -1;
+    const int ts = p->fine_tpr > 0 ? p->fine_tpr % 100 : -1;
     // the residuals read the CSR form (a SELL-32 choice of the autotuner maps to the
     // lanes fitted to the mean row length)
     const int ta = p->spmv_tpr > 0 ? p->spmv_tpr : tpr_of(p->Ah);
@@ -397,7 +447,7 @@ void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s) 
         k_jacobi0<PT, double><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, pick<PT>(p->d_l1h, p->d_l1h32), r, zs);
         PK_LAUNCH();
     } else {
-        gs_forward0<PT, double>(p->fine, ts, r, zs, s);
+        gs_forward0<PT, double>(p->fine, tfw, r, zs, s);
     }
     to_pt<PT>(r, rr, p->nh, s);
     PK_TPR_SWITCH(ta, (k_residual<TPR, PT, PT, PT><<<rows_grid(p->nh, TPR), kBlock, 0, s>>>(
@@ -687,7 +737,9 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
     // problem (P3 32^3, P4 48^3); smoother_layout selects it explicitly.
     // (2 lanes per row, layouts 3 and 102, lost on every measured problem: P3 32^3 FP64
     // 769 vs 467 us; they stay selectable through smoother_layout)
-    const int cand_fine[] = {-1, 0, 4, 8, 16, 104, 108, 116};
+    // 400 + t: t lanes, grid-stride over the resident blocks, the next row's static loads
+    // in flight during the current row's gathers.
+    const int cand_fine[] = {-1, 0, 4, 8, 16, 104, 108, 116, 404, 408, 416};
     const int pick_spmv = tune(cand_spmv, 4, &p->spmv_tpr, [&] { spmv_fine(p, p->d_b, p->w_q, s); });
     p->spmv_tpr = pick_spmv;
     int pick_fine = -1;
@@ -695,9 +747,9 @@ void autotune(pkasp_problem *p, cudaStream_t s) {
         pick_fine = fixed_fine;
     } else if (p->opt.smoother == PKASP_SMOOTHER_SGS) {
         if (p->opt.precond_precision == PKASP_PREC_FP32)
-            pick_fine = tune(cand_fine, 8, &p->fine_tpr, [&] { smoother<float>(p, p->d_b, p->w_zs32, s); });
+            pick_fine = tune(cand_fine, 11, &p->fine_tpr, [&] { smoother<float>(p, p->d_b, p->w_zs32, s); });
         else
-            pick_fine = tune(cand_fine, 8, &p->fine_tpr, [&] { smoother<double>(p, p->d_b, p->w_zs, s); });
+            pick_fine = tune(cand_fine, 11, &p->fine_tpr, [&] { smoother<double>(p, p->d_b, p->w_zs, s); });
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -217,18 +217,20 @@ def test_fp32_preconditioner(pair, torch_cuda):
 @pytest.mark.parametrize("lanes", [4, 8, 16])
 def test_persistent_smoother_matches_phase_launches(pair, torch_cuda, prec, lanes):
     """The whole symmetric sweep in one cooperative launch (grid barriers between colours),
-    and the phases with two rows per lane group, add the same products in the same order
-    as one launch per colour phase with one row per group: bitwise equal results; and
-    equal to the oracle's SGS."""
+    the phases with two rows per lane group, and the grid-stride phases over the resident
+    blocks add the same products in the same order as one
+    launch per colour phase with one row per group: bitwise equal results; and equal to
+    the oracle's SGS."""
     torch = torch_cuda
     _, G, O = pair
     r = torch.tensor(np.random.default_rng(5).standard_normal(G.nh), device="cuda")
     outs = []
-    for layout in (lanes, -lanes, 100 + lanes):
+    for layout in (lanes, -lanes, 100 + lanes, 400 + lanes):
         G.setup(smoother_layout=layout, precond_precision=prec)
         assert G.info.smoother_layout == layout
         outs.append(G.apply_smoother(r))
-    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    for o in outs[1:]:
+        assert torch.equal(outs[0], o)
     if prec == 0:
         O.setup()
         _rel_close(outs[1].cpu().numpy(), O.smoother(r.cpu().numpy()), RTOL_OP)
@@ -240,6 +242,23 @@ def test_persistent_smoother_solve_history(pair, torch_cuda, graph):
     against the oracle: iterations +-1, residual history within 1e-10 ||r_0||."""
     _, G, O = pair
     _setup_both(G, O, smoother_layout=-8, use_graph=graph)
+    ref = O.solve()
+    x, st = G.solve(G.rhs(), hist_cap=600)
+    assert st["status"][0] == 0 and abs(st["iters"][0] - ref["iters"]) <= 1
+    h = st["hist"][:, 0]
+    m = min(len(h), len(ref["hist"]))
+    assert (np.abs(h[:m] - ref["hist"][:m]) / ref["hist"][0]).max() <= RTOL_ITER
+    assert np.linalg.norm(x.cpu().numpy() - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("layout", [404, 408])
+def test_grid_stride_smoother_solve_history(pair, torch_cuda, mode, layout):
+    """PCG with the grid-stride colour phases (additive and multiplicative forms) against
+    the oracle: iterations +-1, residual history within 1e-10 ||r_0||."""
+    _, G, O = pair
+    _setup_both(G, O, smoother_layout=layout, mode=mode)
+    assert G.info.smoother_layout == layout
     ref = O.solve()
     x, st = G.solve(G.rhs(), hist_cap=600)
     assert st["status"][0] == 0 and abs(st["iters"][0] - ref["iters"]) <= 1
