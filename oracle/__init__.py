@@ -40,7 +40,8 @@ class OOpts(C.Structure):
                 ("level_smoother", C.c_int), ("coarse_size", C.c_int),
                 ("max_levels", C.c_int), ("seed", C.c_uint64), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("flexible", C.c_int), ("krylov", C.c_int),
-                ("restart", C.c_int), ("interp_pmax", C.c_int), ("interp_trunc", C.c_int)]
+                ("restart", C.c_int), ("interp_pmax", C.c_int), ("interp_trunc", C.c_int),
+                ("interp_cc", C.c_int)]
 
 
 def lib():
@@ -77,7 +78,7 @@ def lib():
     L.orc_strength.argtypes = [vp, C.c_double, u8p]
     L.orc_pmis.argtypes = [vp, u8p, C.c_uint64, i8p]
     L.orc_extpi.restype = vp
-    L.orc_extpi.argtypes = [vp, u8p, i8p]
+    L.orc_extpi.argtypes = [vp, u8p, i8p, C.c_int]
     L.orc_truncate.restype = vp
     L.orc_truncate.argtypes = [vp, C.c_double, C.c_int]
     L.orc_transpose.restype = vp
@@ -261,12 +262,13 @@ def pmis(a: CSR, strong, stream: int):
     return cf
 
 
-def extpi(a: CSR, strong, cf):
+def extpi(a: CSR, strong, cf, cc=0):
+    """Extended+i interpolation; cc=1 gives the "+cc" form."""
     h = a.handle()
     s = np.ascontiguousarray(strong, dtype=np.uint8)
     if s.size == 0:
         s = np.zeros(1, np.uint8)
-    out = _take(lib().orc_extpi(h, s, np.ascontiguousarray(cf, dtype=np.int8)))
+    out = _take(lib().orc_extpi(h, s, np.ascontiguousarray(cf, dtype=np.int8), int(cc)))
     free_csr(h)
     return out
 
@@ -302,7 +304,7 @@ SOURCE_NONE, SOURCE_SINE = 0, 1
 def default_opts(**kw) -> OOpts:
     o = OOpts(theta=0.25, mode=0, smoother=0, level_smoother=0, coarse_size=256,
               max_levels=25, seed=0, tol=1e-8, max_iter=500, flexible=0, krylov=0, restart=30,
-              interp_pmax=0, interp_trunc=0)
+              interp_pmax=0, interp_trunc=0, interp_cc=0)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

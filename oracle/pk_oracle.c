@@ -1163,9 +1163,13 @@ void orc_pmis(const ocsr *a, const uint8_t *strong, uint64_t stream, int8_t *cf)
 }
 
 /* Extended+i interpolation (De Sterck, Falgout, Nolting & Yang, Numer. Linear Algebra
- * Appl. 15, 2008), without the "+cc" modification and without truncation. For an
- * F-point i with strong C set C_i^s and strong F set F_i^s,
+ * Appl. 15, 2008), without truncation. For an F-point i with strong C set C_i^s and
+ * strong F set F_i^s,
  *   Chat_i = C_i^s u (union over k in F_i^s of C_k^s),
+ * or, with the "+cc" modification (cc = 1; the interpolation of Sec. 1 and Sec. 6.1),
+ *   Chat_i = C_i^s u (union over k in F_i^s with C_k^s n C_i^s empty of C_k^s):
+ * an F neighbour that already shares a strong C point with i adds no C points of its
+ * own; its connections are spread over Chat_i u {i} by the same formula,
  *   abar_kl = a_kl if sign(a_kl) != sign(a_kk) else 0,
  *   d_k = sum_{l in Chat_i u {i}} abar_kl,
  *   atil_ii = a_ii + sum_{n weak, n not in Chat_i} a_in + sum_{k in F_i^s} a_ik abar_ki / d_k,
@@ -1197,7 +1201,17 @@ static int in_sorted(const int32_t *arr, int64_t n, int32_t v) {
     return 0;
 }
 
-ocsr *orc_extpi(const ocsr *a, const uint8_t *strong, const int8_t *cf) {
+/* 1 when k has a strong C point that is also a strong C point of i */
+static int shares_strong_c(const ocsr *a, const uint8_t *strong, const int8_t *cf, int64_t i, int64_t k) {
+    for (int64_t f = a->ptr[k]; f < a->ptr[k + 1]; ++f) {
+        if (!strong[f] || cf[a->col[f]] != 1) continue;
+        for (int64_t e = a->ptr[i]; e < a->ptr[i + 1]; ++e)
+            if (strong[e] && a->col[e] == a->col[f]) return 1;
+    }
+    return 0;
+}
+
+ocsr *orc_extpi(const ocsr *a, const uint8_t *strong, const int8_t *cf, int cc) {
     int64_t n = a->nrows, nc;
     int32_t *ci = coarse_index(n, cf, &nc);
     int64_t cap = 1024, nnz = 0;
@@ -1240,7 +1254,7 @@ ocsr *orc_extpi(const ocsr *a, const uint8_t *strong, const int8_t *cf) {
             if (!strong[e]) continue;
             int64_t k = a->col[e];
             if (cf[k] == 1) hat[nh++] = (int32_t)k;
-            else
+            else if (!cc || !shares_strong_c(a, strong, cf, i, k))
                 for (int64_t f = a->ptr[k]; f < a->ptr[k + 1]; ++f)
                     if (strong[f] && cf[a->col[f]] == 1) hat[nh++] = a->col[f];
         }
@@ -1547,7 +1561,7 @@ int orc_setup(oproblem *P, const oopts *o) {
         int64_t nc = 0;
         for (int64_t i = 0; i < A->nrows; ++i) nc += (L->cf[i] == 1);
         if (nc == 0 || nc == A->nrows) break;
-        L->P = orc_extpi(A, L->strong, L->cf);
+        L->P = orc_extpi(A, L->strong, L->cf, o->interp_cc);
         if (o->interp_trunc > 0 || o->interp_pmax > 0) {
             ocsr *Pt = orc_truncate(L->P, o->interp_trunc / 1000.0, o->interp_pmax);
             orc_csr_free(L->P);

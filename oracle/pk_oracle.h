@@ -30,6 +30,8 @@ typedef struct {
     int restart;         /* FGMRES restart length m */
     int interp_pmax;     /* interpolation truncation: at most this many weights per row (0: no limit) */
     int interp_trunc;    /* interpolation truncation: drop |w| < (interp_trunc / 1000) max|w| */
+    int interp_cc;       /* 1: extended+i+cc (an F neighbour sharing a strong C point with i
+                            adds no C points of its own); 0: extended+i */
 } oopts;
 
 /* problem construction */
@@ -64,7 +66,7 @@ int orc_colour_jp(int64_t n, const int64_t *ptr, const int32_t *col, uint64_t st
 void orc_strength(const ocsr *a, double theta, uint8_t *strong);
 void orc_pmis(const ocsr *a, const uint8_t *strong, uint64_t stream, int8_t *cf);
 ocsr *orc_truncate(const ocsr *p, double tf, int pmax);
-ocsr *orc_extpi(const ocsr *a, const uint8_t *strong, const int8_t *cf);
+ocsr *orc_extpi(const ocsr *a, const uint8_t *strong, const int8_t *cf, int cc);
 ocsr *orc_transpose(const ocsr *a);
 ocsr *orc_spgemm(const ocsr *a, const ocsr *b);
 ocsr *orc_rap(const ocsr *a, const ocsr *p);

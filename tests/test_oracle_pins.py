@@ -378,6 +378,67 @@ def test_extpi_preserves_constants_and_pattern(oracle_mod):
         assert Ps.data[Ps.indptr[i]] == 1.0
 
 
+@pytest.mark.parametrize("theta", [0.25, 0.5])
+def test_extpi_cc_pattern_constants_and_agreement(oracle_mod, theta):
+    """Extended+i+cc (Sec. 1, Sec. 6.1): row i interpolates from C_i^s and the strong C
+    points of those strong F neighbours k that share no strong C point with i (sets
+    built here from the strength graph); constants are reproduced on a zero-row-sum
+    matrix (every F row's weights sum to 1); rows where no F
+    neighbour shares a C point equal the extended+i rows bitwise; and the rule removes
+    entries on this matrix."""
+    A = _p1_matrix(oracle_mod, 6, dirichlet=False)
+    s = oracle_mod.strength(A, theta)
+    cf = oracle_mod.pmis(A, s, 11)
+    P0 = oracle_mod.extpi(A, s, cf).to_scipy()
+    Pc = oracle_mod.extpi(A, s, cf, cc=1).to_scipy()
+    S = A.to_scipy()
+    st = s.astype(bool)
+    cidx = np.cumsum(cf == 1) - 1
+
+    def strong_nb(i):
+        cols = S.indices[S.indptr[i]:S.indptr[i + 1]]
+        return [int(j) for j in cols[st[S.indptr[i]:S.indptr[i + 1]]] if j != i]
+
+    removed = 0
+    for i in np.nonzero(cf == -1)[0]:
+        ci = {j for j in strong_nb(i) if cf[j] == 1}
+        want, shared_any = set(ci), False
+        for k in strong_nb(i):
+            if cf[k] != -1:
+                continue
+            ck = {j for j in strong_nb(k) if cf[j] == 1}
+            if ck & ci:
+                shared_any = True
+            else:
+                want |= ck
+        got = Pc.indices[Pc.indptr[i]:Pc.indptr[i + 1]]
+        assert sorted(got.tolist()) == sorted(cidx[j] for j in want)
+        w = Pc.data[Pc.indptr[i]:Pc.indptr[i + 1]]
+        if len(w):
+            assert abs(w.sum() - 1.0) <= 1e-12
+        r0 = slice(P0.indptr[i], P0.indptr[i + 1])
+        if not shared_any:
+            assert np.array_equal(P0.indices[r0], got) and np.array_equal(P0.data[r0], w)
+        removed += (P0.indptr[i + 1] - P0.indptr[i]) - len(got)
+    assert removed > 0
+    for i in np.nonzero(cf == 1)[0]:
+        assert list(Pc.indices[Pc.indptr[i]:Pc.indptr[i + 1]]) == [cidx[i]]
+
+
+def test_extpi_cc_hierarchy_converges_with_lower_complexity(oracle_mod):
+    """The aux-space solve with the +cc hierarchy reaches 1e-8, and the P1 hierarchy's
+    operator complexity is no larger than with extended+i."""
+    xyz, t = _mesh(6)
+    P = oracle_mod.Problem(xyz, t, 2, kappa_lognormal(t.shape[0], 1))
+    out = {}
+    for cc in (0, 1):
+        P.setup(coarse_size=20, interp_cc=cc)
+        ref = P.solve()
+        assert ref["status"] == 0
+        out[cc] = sum(P.level(l)["A"].nnz for l in range(P.levels()))
+    assert out[1] <= out[0]
+
+
 @pytest.mark.parametrize("tf,pmax", [(0.0, 0), (0.2, 0), (0.0, 3), (0.3, 4)])
 def test_interpolation_truncation_properties(oracle_mod, tf, pmax):
     """Truncation keeps what its definition fixes: no row longer than pmax; every kept
