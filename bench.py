@@ -242,6 +242,8 @@ def main():
                     help="pin the fine smoother layout (pkasp_options.smoother_layout) instead of "
                          "autotuning it; for profiler runs, under which the autotuner's timings "
                          "are distorted")
+    ap.add_argument("--smoother-layout-fp32", type=int, default=0,
+                    help="the same for the FP32-preconditioner solves")
     ap.add_argument("--mesh-n", type=int, default=0,
                     help="cubes per side of the mesh instead of the workload's own (a smaller case "
                          "of the same kernels for profiler captures; the JSON line states the size)")
@@ -382,13 +384,16 @@ def main():
                  if p3 else None,
                  "peak_source": src, "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms}
     # the mixed-precision variant of the same solve: FP32 smoother / I_P / AMG, FP64 flexible CG
-    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, precond_precision=1, use_graph=0 if args.eager else 1)
+    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, precond_precision=1, use_graph=0 if args.eager else 1,
+            smoother_layout=args.smoother_layout_fp32)
     for _ in range(2):
         st32 = step()
     ms32 = []
+    torch.cuda.nvtx.range_push("fp32_solves")  # lets ncu --nvtx-include select them
     for _ in range(3):
         st32 = step()
         ms32.append(st32["solve_ms"])
+    torch.cuda.nvtx.range_pop()
     extra32 = {"fp32_precond_time_to_solution_s": min(ms32) / 1e3, "fp32_precond_iterations": st32["iters"][0],
                "fp32_precond_true_rel_residual": st32["true_rel"][0],
                "fp32_precond_speedup_vs_fp64": sol_s / (min(ms32) / 1e3)}
@@ -485,11 +490,12 @@ def run_theta_study(args):
 
 
 def run_cop_study(args):
-    """Operator complexities against the paper's Table 6 (PMIS + extended+i, theta 0.25):
-    plain AMG on A_h (sum nnz(A_l) / nnz(A_h)), the P1 AMG of the auxiliary space
-    (relative to A_H) and the whole auxiliary-space hierarchy relative to A_h ("GAMG":
-    (nnz(A_h) + sum nnz of the P1 levels) / nnz(A_h)); without truncation and with at most
-    4 interpolation weights per row. Iterations and times beside them. One JSON line."""
+    """Operator complexities against the paper's Table 6 (PMIS, theta 0.25): plain AMG on
+    A_h (sum nnz(A_l) / nnz(A_h)), the P1 AMG of the auxiliary space (relative to A_H) and
+    the whole auxiliary-space hierarchy relative to A_h ("GAMG": (nnz(A_h) + sum nnz of
+    the P1 levels) / nnz(A_h)); with extended+i and extended+i+cc interpolation (the
+    paper's), each without truncation and with at most 4 interpolation weights per row.
+    Iterations and times beside them. One JSON line."""
     import torch
 
     from paper_1204_2586_gb300 import Problem
@@ -501,10 +507,11 @@ def run_cop_study(args):
         G = Problem(xyz, t, k)
         b = G.rhs()
         nnz_h = int(G.info.nnz_h)
-        for pmax in (0, 4):
+        for cc, pmax in ((0, 0), (0, 4), (1, 0), (1, 4)):
             for mode, name in ((0, "aux_space_additive"), (2, "plain_amg")):
                 t0 = time.perf_counter()
-                G.setup(theta=0.25, mode=mode, level_smoother=LEVEL_SMOOTHER, interp_pmax=pmax, max_iter=2000)
+                G.setup(theta=0.25, mode=mode, level_smoother=LEVEL_SMOOTHER, interp_pmax=pmax, interp_cc=cc,
+                        max_iter=2000)
                 torch.cuda.synchronize()
                 setup_s = time.perf_counter() - t0
                 x = torch.zeros_like(b)
@@ -513,7 +520,8 @@ def run_cop_study(args):
                 _, st = G.solve(b, x, raise_on_fail=False)
                 info = G.info
                 lev_nnz = [int(info.level_nnz[l]) for l in range(info.levels)]
-                row = {"k": k, "n": n, "n_h": G.nh, "interp_pmax": pmax, "method": name,
+                row = {"k": k, "n": n, "n_h": G.nh, "interp": "ext+i+cc" if cc else "ext+i",
+                       "interp_pmax": pmax, "method": name,
                        "iterations": st["iters"][0], "solve_s": st["solve_ms"] / 1e3, "setup_s": setup_s,
                        "levels": int(info.levels)}
                 if mode == 2:

@@ -103,7 +103,11 @@ typedef struct {
     int interp_trunc;     /* AMG interpolation truncation: drop weights below
                              (interp_trunc / 1000) x the row's largest |w|, 0..999 [0];
                              with either, kept weights are scaled to the row's sum */
-    int reserved[2];
+    int interp_cc;        /* 1: extended+i+cc interpolation, the form Sec. 1 and Sec. 6.1
+                             name: a strong F neighbour k of i adds its strong C points to
+                             i's interpolatory set only when k shares no strong C point
+                             with i; 0: extended+i [0] */
+    int reserved[1];
 } pkasp_options;
 
 /* Problem sizes after assembly and (for the AMG entries) after setup. */

@@ -31,7 +31,7 @@ class pkasp_options(C.Structure):
                 ("flexible", C.c_int), ("precond_precision", C.c_int), ("use_graph", C.c_int),
                 ("spmv_threads", C.c_int), ("smoother_layout", C.c_int), ("krylov", C.c_int),
                 ("restart", C.c_int), ("interp_pmax", C.c_int), ("interp_trunc", C.c_int),
-                ("reserved", C.c_int * 2)]
+                ("interp_cc", C.c_int), ("reserved", C.c_int * 1)]
 
 
 class pkasp_info(C.Structure):

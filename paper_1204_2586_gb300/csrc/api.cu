@@ -77,6 +77,7 @@ void pkasp_default_options(pkasp_options *o) {
     o->restart = 30;
     o->interp_pmax = 0;
     o->interp_trunc = 0;
+    o->interp_cc = 0;
 }
 
 int pkasp_last_error(char *buf, size_t n) {
@@ -249,6 +250,7 @@ int pkasp_setup(pkasp_problem *p, const pkasp_options *opt, pkasp_stream_t strea
         return set_error(PKASP_EINVAL, "spmv_threads must be 0, 4, 8, 16 or 32");
     if (o.interp_pmax < 0 || o.interp_trunc < 0 || o.interp_trunc > 999)
         return set_error(PKASP_EINVAL, "interp_pmax must be >= 0 and interp_trunc 0..999");
+    if (o.interp_cc != 0 && o.interp_cc != 1) return set_error(PKASP_EINVAL, "interp_cc must be 0 or 1");
     if (o.krylov != PKASP_KRYLOV_CG && o.krylov != PKASP_KRYLOV_FGMRES)
         return set_error(PKASP_EINVAL, "krylov must be PKASP_KRYLOV_CG or PKASP_KRYLOV_FGMRES");
     if (o.krylov == PKASP_KRYLOV_FGMRES && (o.restart < 1 || o.restart > 256))

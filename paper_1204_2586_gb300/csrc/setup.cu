@@ -280,8 +280,11 @@ __global__ void k_flag_c(int64_t n, const int8_t *__restrict__ cf, int64_t *__re
 }
 
 // ---------------------------------------------------------------------------------
-// Extended+i interpolation (De Sterck, Falgout, Nolting & Yang 2008), no "+cc", no
-// truncation; a strong F neighbour k with zero denominator is lumped into the diagonal.
+// Extended+i interpolation (De Sterck, Falgout, Nolting & Yang 2008), no truncation; a
+// strong F neighbour k with zero denominator is lumped into the diagonal. With cc = 1
+// (extended+i+cc, the form Sec. 1 and Sec. 6.1 name) a strong F neighbour k that shares
+// a strong C point with i adds none of its own C points to the interpolatory set; the
+// weights then follow from the same formula over that smaller set.
 // ---------------------------------------------------------------------------------
 __global__ void k_extpi_ub(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
                            const uint8_t *__restrict__ strong, const int8_t *__restrict__ cf,
@@ -319,10 +322,22 @@ __device__ void sort_unique_i32(int32_t *a, int64_t &m) {
     m = u;
 }
 
+// 1 when k has a strong C point that is also a strong C point of i
+__device__ bool shares_strong_c(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                const uint8_t *__restrict__ strong, const int8_t *__restrict__ cf, int64_t i,
+                                int32_t k) {
+    for (int64_t f = ptr[k]; f < ptr[k + 1]; ++f) {
+        if (!strong[f] || cf[col[f]] != 1) continue;
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e)
+            if (strong[e] && col[e] == col[f]) return true;
+    }
+    return false;
+}
+
 __global__ void k_extpi_hat(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
                             const uint8_t *__restrict__ strong, const int8_t *__restrict__ cf,
                             const int64_t *__restrict__ ub_off, int32_t *__restrict__ scratch,
-                            int64_t *__restrict__ cnt) {
+                            int64_t *__restrict__ cnt, int cc) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (cf[i] == 1) {
@@ -335,7 +350,7 @@ __global__ void k_extpi_hat(int64_t n, const int64_t *__restrict__ ptr, const in
         if (!strong[e]) continue;
         int32_t k = col[e];
         if (cf[k] == 1) h[m++] = k;
-        else
+        else if (!cc || !shares_strong_c(ptr, col, strong, cf, i, k))
             for (int64_t f = ptr[k]; f < ptr[k + 1]; ++f)
                 if (strong[f] && cf[col[f]] == 1) h[m++] = col[f];
     }
@@ -911,7 +926,7 @@ __global__ void k_trunc_fill(int64_t n, const int64_t *__restrict__ ptr, const i
 }
 
 bool coarsen(DevPool &pool, Level &L, double theta, uint64_t pmis_stream, DCSR &Ac, cudaStream_t s,
-             double trunc_factor, int pmax) {
+             double trunc_factor, int pmax, int cc) {
     const DCSR &A = L.A;
     const int64_t n = A.n;
     L.strong = pool.get<uint8_t>(A.nnz > 0 ? A.nnz : 1);
@@ -938,7 +953,7 @@ bool coarsen(DevPool &pool, Level &L, double theta, uint64_t pmis_stream, DCSR &
             if (tot > ((int64_t)1 << 31)) fail(PKASP_ENOMEM, "interpolation scratch above 2^31 entries");
             int32_t *scr = tmp.get<int32_t>(tot > 0 ? tot : 1);
             int64_t *cnt = tmp.get<int64_t>(n + 1);
-            k_extpi_hat<<<blocks_for(n, 128), 128, 0, s>>>(n, A.ptr, A.col, L.strong, L.cf, ub, scr, cnt);
+            k_extpi_hat<<<blocks_for(n, 128), 128, 0, s>>>(n, A.ptr, A.col, L.strong, L.cf, ub, scr, cnt, cc);
             PK_LAUNCH();
             exclusive_scan(cnt, n, s);
             int64_t pnnz = read_i64(cnt + n, s);

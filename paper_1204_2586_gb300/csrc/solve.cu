@@ -21,7 +21,7 @@ namespace pk {
 void build_split(DevPool &pool, const DCSR &A, uint64_t stream, bool want32, DSplit &sp, cudaStream_t s);
 double *row_l1(DevPool &pool, const DCSR &A, cudaStream_t s);
 bool coarsen(DevPool &pool, Level &L, double theta, uint64_t pmis_stream, DCSR &Ac, cudaStream_t s,
-             double trunc_factor, int pmax);
+             double trunc_factor, int pmax, int cc);
 void coarse_inverse(DevPool &pool, const DCSR &A, double **inv, cudaStream_t s);
 
 namespace {
@@ -794,7 +794,8 @@ void setup_device(pkasp_problem *p, cudaStream_t s) {
         L.l1 = row_l1(pool, L.A, s);
         if (L.A.n <= o.coarse_size || l + 1 >= maxl) break;
         DCSR Ac;
-        if (!coarsen(pool, L, o.theta, stream_pmis(o.seed, l), Ac, s, o.interp_trunc / 1000.0, o.interp_pmax))
+        if (!coarsen(pool, L, o.theta, stream_pmis(o.seed, l), Ac, s, o.interp_trunc / 1000.0, o.interp_pmax,
+                     o.interp_cc))
             break;
         p->lev.emplace_back();
         p->lev[l + 1].A = Ac;

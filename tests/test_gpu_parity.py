@@ -86,17 +86,19 @@ def _setup_both(G, O, **kw):
     okw = {k: v for k, v in kw.items() if k in ("theta", "mode", "smoother", "level_smoother",
                                                "coarse_size", "max_levels", "seed", "tol", "max_iter",
                                                "flexible", "krylov", "restart", "interp_pmax",
-                                               "interp_trunc")}
+                                               "interp_trunc", "interp_cc")}
     O.setup(**okw)
 
 
-@pytest.mark.parametrize("mode,pmax,trunc", [(0, 0, 0), (2, 0, 0), (0, 4, 200), (2, 3, 0)])
-def test_colourings_and_hierarchy(pair, mode, pmax, trunc):
+@pytest.mark.parametrize("mode,pmax,trunc,cc", [(0, 0, 0, 0), (2, 0, 0, 0), (0, 4, 200, 0), (2, 3, 0, 0),
+                                                (0, 0, 0, 1), (2, 0, 0, 1), (2, 4, 0, 1)])
+def test_colourings_and_hierarchy(pair, mode, pmax, trunc, cc):
     """Colourings, strength flags and C/F splittings are integer decisions: bit-exact.
     mode 2 (plain AMG) builds the hierarchy on A_h itself; pmax / trunc truncate the
-    interpolation (the kept pattern is an integer decision too)."""
+    interpolation and cc selects extended+i+cc (the kept pattern is an integer decision
+    too)."""
     _, G, O = pair
-    _setup_both(G, O, mode=mode, interp_pmax=pmax, interp_trunc=trunc)
+    _setup_both(G, O, mode=mode, interp_pmax=pmax, interp_trunc=trunc, interp_cc=cc)
     if mode == 2:
         assert G.info.level_rows[0] == G.nh
     gc, gn = G.colours(-1)
@@ -147,14 +149,15 @@ def test_preconditioner_pieces(pair, torch_cuda, mode, sm, lsm):
     _rel_close(G.apply_prec(rt).cpu().numpy(), O.apply_prec(r), 1e-11)
 
 
-@pytest.mark.parametrize("mode,graph,pmax", [(0, 1, 0), (0, 0, 0), (1, 1, 0), (1, 0, 0), (2, 1, 0), (2, 0, 0),
-                                             (0, 1, 4), (2, 1, 4)])
-def test_pcg_history(pair, torch_cuda, mode, graph, pmax):
+@pytest.mark.parametrize("mode,graph,pmax,cc", [(0, 1, 0, 0), (0, 0, 0, 0), (1, 1, 0, 0), (1, 0, 0, 0),
+                                                (2, 1, 0, 0), (2, 0, 0, 0), (0, 1, 4, 0), (2, 1, 4, 0),
+                                                (0, 1, 0, 1), (2, 1, 0, 1)])
+def test_pcg_history(pair, torch_cuda, mode, graph, pmax, cc):
     """Per-iteration residual norms match the oracle's to 1e-10 relative to ||r_0||
     (CG amplifies rounding differences as ||r_k|| falls, so agreement relative to
     ||r_k|| itself is not attainable near convergence); iteration counts within +-1."""
     _, G, O = pair
-    _setup_both(G, O, mode=mode, use_graph=graph, interp_pmax=pmax)
+    _setup_both(G, O, mode=mode, use_graph=graph, interp_pmax=pmax, interp_cc=cc)
     ref = O.solve()
     assert ref["status"] == 0
     b = G.rhs()
