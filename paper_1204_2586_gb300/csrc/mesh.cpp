@@ -430,7 +430,8 @@ void build_dofmap(const HostMesh &M, DofMap &D) {
             int32_t j = D.elem_vdof[t * 4 + a];
             if (m4[4 * m + a] > 0 && j >= 0) ent[c++] = {j, (double)m4[4 * m + a] / k};
         }
-        std::sort(ent, ent + c);
+        for (int q = 1; q < c; ++q)  // at most 4 entries: insertion sort by column
+            for (int r = q; r > 0 && ent[r].first < ent[r - 1].first; --r) std::swap(ent[r], ent[r - 1]);
         for (int q = 0; q < c; ++q) {
             P.col.push_back(ent[q].first);
             P.val.push_back(ent[q].second);

@@ -256,11 +256,6 @@ __global__ void k_add_div(int64_t n, const PT *__restrict__ r, const PT *__restr
     if (i < n) x[i] += r[i] / d[i];
 }
 
-int split_tpr(const DSplit &sp, int64_t n) {
-    double m = n > 0 ? (double)std::max(sp.nnz_l, sp.nnz_u) / (double)n : 1.0;
-    return tpr_for(m);
-}
-
 // ---------------------------------------------------------------------------------
 // V(1,1)-cycle on level l (vectors b, x, r of each level)
 // ---------------------------------------------------------------------------------

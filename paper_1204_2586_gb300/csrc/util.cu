@@ -103,12 +103,6 @@ __global__ void k_scan_add(int64_t *d, int64_t n, const int64_t *tile_off) {
     if (i < n) d[i] += tile_off[i / kScanTile];
 }
 
-__global__ void k_set_total(int64_t *d, int64_t n, const int64_t *tile_sums, int64_t ntiles) {
-    // d[n] = d[n-1] + (last element's original value) is not available any more, so the
-    // total is the exclusive offset of the last tile plus that tile's sum
-    if (threadIdx.x == 0 && blockIdx.x == 0) d[n] = tile_sums[ntiles - 1];
-}
-
 void scan_rec(int64_t *d, int64_t n, cudaStream_t s, int64_t *total_out_dev) {
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     int64_t *sums = nullptr;
