@@ -128,6 +128,28 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int64_t n, const int64_t *__res
     if (ok && sub == 0) y[row] = (YT)s;
 }
 
+// Restriction fused with the l1-Jacobi pre-smoothing step from zero of the level it
+// feeds: b = R x (as k_spmv) and x_c = b / l1 (as k_jacobi0) in one pass, bitwise the two
+// kernels' results.
+template <int TPR, typename A, typename VT, typename XT, typename PT>
+__global__ void __launch_bounds__(kBlock) k_restrict_jacobi0(int64_t n, const int64_t *__restrict__ ptr,
+                                                             const int32_t *__restrict__ col,
+                                                             const VT *__restrict__ val, const XT *__restrict__ x,
+                                                             const PT *__restrict__ l1, PT *__restrict__ b,
+                                                             PT *__restrict__ xc) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = row < n;
+    int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+    A s = row_dot<TPR, A>(lo, hi, sub, col, val, x);
+    if (ok && sub == 0) {
+        const PT bi = (PT)s;
+        b[row] = bi;
+        xc[row] = bi / l1[row];
+    }
+}
+
 // r = b - A x
 template <int TPR, typename A, typename VT, typename T>
 __global__ void __launch_bounds__(kBlock) k_residual(int64_t n, const int64_t *__restrict__ ptr,

@@ -267,7 +267,30 @@ template <typename PT>
 PT *lv_r(Level &L) { return pickw<PT>(L.r, L.r32); }
 
 template <typename PT>
-void vcycle(pkasp_problem *p, int l, cudaStream_t s) {
+void vcycle(pkasp_problem *p, int l, cudaStream_t s, bool pre_done = false);
+
+// b_l = R x (R = I_P^T into level 0, or level l-1's restriction); with l1-Jacobi level
+// smoothing on a level that is not the coarsest, the same pass also takes the
+// pre-smoothing step from zero, x_l = b_l / l1 (returns true then).
+template <typename PT, typename XT>
+bool restrict_to(pkasp_problem *p, const DCSR &R, const XT *x, int l, cudaStream_t s) {
+    Level &L = p->lev[l];
+    const bool fuse = p->opt.level_smoother == PKASP_SMOOTHER_L1JACOBI && l < (int)p->lev.size() - 1;
+    if (!fuse || R.n == 0) {
+        spmv<PT, PT>(R, x, lv_b<PT>(L), tpr_of(R), s);
+        return false;
+    }
+    PK_TPR_SWITCH(tpr_of(R), (k_restrict_jacobi0<TPR, PT, PT, XT, PT><<<rows_grid(R.n, TPR), kBlock, 0, s>>>(
+                                 R.n, R.ptr, R.col, pick<PT>(R.val, R.val32), x, pick<PT>(L.l1, L.l132),
+                                 lv_b<PT>(L), lv_x<PT>(L))));
+    PK_LAUNCH();
+    return true;
+}
+
+// V(1,1)-cycle on level l; pre_done: the pre-smoothing step from zero was taken by the
+// restriction that produced b_l
+template <typename PT>
+void vcycle(pkasp_problem *p, int l, cudaStream_t s, bool pre_done) {
     Level &L = p->lev[l];
     const int64_t n = L.A.n;
     if (l == (int)p->lev.size() - 1) {
@@ -279,8 +302,11 @@ void vcycle(pkasp_problem *p, int l, cudaStream_t s) {
     const bool jac = p->opt.level_smoother == PKASP_SMOOTHER_L1JACOBI;
     const int ta = tpr_of(L.A), ts = -1;  // lanes per colour phase chosen per colour
     if (jac) {
-        k_jacobi0<PT, PT><<<elem_grid(n), kBlock, 0, s>>>(n, pick<PT>(L.l1, L.l132), lv_b<PT>(L), lv_x<PT>(L));
-        PK_LAUNCH();
+        if (!pre_done) {
+            k_jacobi0<PT, PT><<<elem_grid(n), kBlock, 0, s>>>(n, pick<PT>(L.l1, L.l132), lv_b<PT>(L),
+                                                              lv_x<PT>(L));
+            PK_LAUNCH();
+        }
     } else {
         gs_forward0<PT, PT>(L.sp, ts, lv_b<PT>(L), lv_x<PT>(L), s);
     }
@@ -289,8 +315,8 @@ void vcycle(pkasp_problem *p, int l, cudaStream_t s) {
                           lv_r<PT>(L))));
     PK_LAUNCH();
     Level &C = p->lev[l + 1];
-    spmv<PT, PT>(L.R, lv_r<PT>(L), lv_b<PT>(C), tpr_of(L.R), s);
-    vcycle<PT>(p, l + 1, s);
+    const bool pd = restrict_to<PT>(p, L.R, (const PT *)lv_r<PT>(L), l + 1, s);
+    vcycle<PT>(p, l + 1, s, pd);
     const int tp = tpr_of(L.P);
     PK_TPR_SWITCH(tp, (k_prolong_inplace<TPR, PT><<<rows_grid(n, TPR), kBlock, 0, s>>>(
                           n, L.P.ptr, L.P.col, pick<PT>(L.P.val, L.P.val32), lv_x<PT>(C), lv_x<PT>(L))));
@@ -395,9 +421,8 @@ void smoother(pkasp_problem *p, const double *r, PT *zs, cudaStream_t s) {
 
 template <typename PT>
 void restrict_vcycle(pkasp_problem *p, const double *r, cudaStream_t s) {
-    Level &L0 = p->lev[0];
-    spmv<PT, PT>(p->PiT, r, lv_b<PT>(L0), tpr_of(p->PiT), s);
-    vcycle<PT>(p, 0, s);
+    const bool pd = restrict_to<PT>(p, p->PiT, r, 0, s);
+    vcycle<PT>(p, 0, s, pd);
 }
 
 // z = B r
@@ -448,8 +473,8 @@ void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s) 
     PK_TPR_SWITCH(ta, (k_residual<TPR, PT, PT, PT><<<rows_grid(p->nh, TPR), kBlock, 0, s>>>(
                           p->nh, p->Ah.ptr, p->Ah.col, pick<PT>(p->Ah.val, p->Ah.val32), rr, zs, t)));
     PK_LAUNCH();
-    spmv<PT, PT>(p->PiT, (const PT *)t, lv_b<PT>(L0), tpr_of(p->PiT), s);
-    vcycle<PT>(p, 0, s);
+    const bool pd = restrict_to<PT>(p, p->PiT, (const PT *)t, 0, s);
+    vcycle<PT>(p, 0, s, pd);
     k_prolong_add<PT, PT><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, p->Pi.ptr, p->Pi.col,
                                                               pick<PT>(p->Pi.val, p->Pi.val32), lv_x<PT>(L0),
                                                               zs, zs);

@@ -135,8 +135,12 @@ def test_pmis_bit_exact_on_oracle_strength(pair, torch_cuda):
         assert np.array_equal(cf_g, cf_o)
 
 
-@pytest.mark.parametrize("mode,sm,lsm", [(0, 0, 0), (0, 1, 1), (1, 0, 0), (1, 1, 0), (2, 0, 0), (2, 0, 1)])
+@pytest.mark.parametrize("mode,sm,lsm", [(0, 0, 0), (0, 1, 1), (0, 0, 1), (1, 0, 0), (1, 1, 0), (1, 0, 1),
+                                         (2, 0, 0), (2, 0, 1)])
 def test_preconditioner_pieces(pair, torch_cuda, mode, sm, lsm):
+    """S_k, one V-cycle and the whole preconditioner against the oracle. With l1-Jacobi
+    levels (lsm = 1) every restriction also takes the level's first smoothing step
+    (fused kernel)."""
     torch = torch_cuda
     _, G, O = pair
     _setup_both(G, O, mode=mode, smoother=sm, level_smoother=lsm)
