@@ -251,12 +251,16 @@ def main():
                     help="launch the same kernels without the CUDA graph (profilers cannot see "
                          "kernels inside graphs that hold conditional nodes)")
     args = ap.parse_args()
-    if args.mesh_n and args.workload != BATCHED["name"]:
-        ap.error("--mesh-n applies to the multi-RHS workload only")
+    if args.mesh_n and args.workload not in SINGLE and args.workload != BATCHED["name"]:
+        ap.error("--mesh-n applies to the p3, p4 and multi-RHS workloads")
     if args.warmup < 3:
         args.warmup = 3
     if args.workload in SINGLE:
         WORKLOAD, CONFIG = SINGLE[args.workload]
+        if args.mesh_n:  # a smaller case of the same workload (profiler captures)
+            WORKLOAD = dict(WORKLOAD, n=args.mesh_n)
+            CONFIG = dict(CONFIG, workload=f"{CONFIG['workload']} -- REDUCED to {args.mesh_n}^3 cubes "
+                                           "(--mesh-n), not the named workload")
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -367,7 +371,7 @@ def main():
     peak = hbm if hbm else 6800.0
     src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback"
     s_ach = smoother_bytes / (smoother_ms / 1e3) / 1e9
-    p3 = WORKLOAD["name"] == "p3_n32"
+    p3 = WORKLOAD["name"] == "p3_n32" and WORKLOAD["n"] == 32
     roof = {"bound": "hbm", "kernel": "k_gs_phase (colour phases of the fine SGS S_k, FP64)",
             "achieved": s_ach, "peak": peak, "unit": "GB/s", "frac": s_ach / peak, "traffic": None,
             "frac_of_nominal_8000": s_ach / NOMINAL_HBM_GBS,
