@@ -220,6 +220,12 @@ int pkasp_setup(pkasp_problem *p, const pkasp_options *opt, pkasp_stream_t strea
 int pkasp_solve(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld,
                 pkasp_stats *st, pkasp_stream_t stream);
 
+/* pkasp_solve from the initial guess x0 = 0: x is written, never read (a host x is not
+ * uploaded; its columns are zeroed on the device), so a caller that starts from zero
+ * moves only b to the device. Same conventions and results as pkasp_solve with a zero x. */
+int pkasp_solve_from_zero(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld,
+                          pkasp_stats *st, pkasp_stream_t stream);
+
 /* Adjoint solve A_h^T lambda = g (A_h is symmetric, so this is the same operator and
  * preconditioner): lambda holds the initial guess on entry. Same conventions as
  * pkasp_solve. */

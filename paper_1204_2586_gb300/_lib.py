@@ -71,6 +71,7 @@ SIGNATURES = [
     ("pkasp_set_kappa", C.c_int, [vp, vp, vp]),
     ("pkasp_setup", C.c_int, [vp, C.POINTER(pkasp_options), vp]),
     ("pkasp_solve", C.c_int, [vp, vp, vp, C.c_int, i64, C.POINTER(pkasp_stats), vp]),
+    ("pkasp_solve_from_zero", C.c_int, [vp, vp, vp, C.c_int, i64, C.POINTER(pkasp_stats), vp]),
     ("pkasp_solve_adjoint", C.c_int, [vp, vp, vp, C.c_int, i64, C.POINTER(pkasp_stats), vp]),
     ("pkasp_grad_kappa", C.c_int, [vp, vp, vp, vp, vp]),
     ("pkasp_destroy", C.c_int, [vp]),

@@ -273,7 +273,7 @@ int pkasp_setup(pkasp_problem *p, const pkasp_options *opt, pkasp_stream_t strea
 }
 
 static int solve_common(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld, pkasp_stats *st,
-                        pkasp_stream_t stream) {
+                        pkasp_stream_t stream, bool from_zero = false) {
     if (!p || !b || !x) return set_error(PKASP_EINVAL, "NULL argument");
     if (!p->have_setup) return set_error(PKASP_ESTATE, "pkasp_setup must precede pkasp_solve");
     if (ncols < 1 || ncols > PKASP_MAX_COLS) return set_error(PKASP_EINVAL, "ncols must be 1..64");
@@ -296,8 +296,11 @@ static int solve_common(pkasp_problem *p, const double *b, double *x, int ncols,
             bb = p->stage_b;
         }
         if (!xd) {
-            PK_CUDA(cudaMemcpyAsync(p->stage_x, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
             xx = p->stage_x;
+            if (from_zero) PK_CUDA(cudaMemsetAsync(xx, 0, sizeof(double) * n, s));
+            else PK_CUDA(cudaMemcpyAsync(xx, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        } else if (from_zero) {
+            PK_CUDA(cudaMemsetAsync(xx, 0, sizeof(double) * n, s));
         }
         int rc = pk::solve_device(p, bb, xx, ncols, ld, st, s);
         if (!xd) {
@@ -315,6 +318,11 @@ static int solve_common(pkasp_problem *p, const double *b, double *x, int ncols,
 int pkasp_solve(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld, pkasp_stats *st,
                 pkasp_stream_t stream) {
     return solve_common(p, b, x, ncols, ld, st, stream);
+}
+
+int pkasp_solve_from_zero(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld,
+                          pkasp_stats *st, pkasp_stream_t stream) {
+    return solve_common(p, b, x, ncols, ld, st, stream, true);
 }
 
 int pkasp_solve_adjoint(pkasp_problem *p, const double *g, double *lambda, int ncols, int64_t ld,

@@ -131,8 +131,9 @@ class Problem:
         self.opts = o
         return self
 
-    def solve(self, b, x=None, hist_cap=0, stream=None, raise_on_fail=True):
+    def solve(self, b, x=None, hist_cap=0, stream=None, raise_on_fail=True, from_zero=False):
         """Solve A_h x = b; b, x are CUDA tensors [n_h] or [n_h, ncols] (or host arrays).
+        from_zero: start from x0 = 0 without reading x (pkasp_solve_from_zero).
         Returns (x, stats dict)."""
         import torch
 
@@ -150,7 +151,8 @@ class Problem:
             st.hist_cap = hist_cap
         bp = _ptr(b) if isinstance(b, torch.Tensor) else b.ctypes.data
         xp = _ptr(x) if isinstance(x, torch.Tensor) else x.ctypes.data
-        rc = L.load().pkasp_solve(self.h, bp, xp, ncols, ld, C.byref(st), _stream(stream))
+        fn = L.load().pkasp_solve_from_zero if from_zero else L.load().pkasp_solve
+        rc = fn(self.h, bp, xp, ncols, ld, C.byref(st), _stream(stream))
         if rc not in (L.PKASP_OK, L.PKASP_ENOTCONV, L.PKASP_EBREAKDOWN) or (rc != L.PKASP_OK and raise_on_fail):
             L.check(rc)
         out = dict(rc=rc, iters=list(st.iters[:ncols]), status=list(st.status[:ncols]),

@@ -132,3 +132,32 @@ def test_set_kappa_reassembles(gpu, oracle_mod):
     ref = O.solve()
     assert abs(st["iters"][0] - ref["iters"]) <= 1
     G.close()
+
+
+@pytest.mark.parametrize("ncols", [1, 5])
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_solve_from_zero_never_reads_x(gpu, ncols, where):
+    """pkasp_solve_from_zero starts from x0 = 0 whatever x holds (NaN here): the same
+    result, bitwise, as pkasp_solve with a zero x, for host and device buffers."""
+    torch = gpu
+    from paper_1204_2586_gb300 import Problem
+    from paper_1204_2586_gb300.inputs import rhs_normal
+
+    G = Problem(*kuhn_mesh(5, 0.2, 0), 2)
+    G.setup()
+    B = np.ascontiguousarray(rhs_normal(G.nh, ncols, 7))
+    if ncols == 1:
+        B = np.ascontiguousarray(B[:, 0])
+    if where == "device":
+        b = torch.tensor(B, device="cuda")
+        x0 = torch.zeros_like(b)
+        xn = torch.full_like(b, float("nan"))
+    else:
+        b, x0, xn = B, np.zeros_like(B), np.full_like(B, np.nan)
+    ref, st0 = G.solve(b, x0)
+    out, st1 = G.solve(b, xn, from_zero=True)
+    ref = ref.cpu().numpy() if where == "device" else ref
+    out = out.cpu().numpy() if where == "device" else out
+    assert np.array_equal(ref, out)
+    assert st0["iters"] == st1["iters"] and all(s == 0 for s in st1["status"])
+    G.close()
