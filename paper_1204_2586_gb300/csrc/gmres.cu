@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kBlock) kg_spmv_w(int64_t n, RowOp A, const do
 struct Gmres {
     static void init(pkasp_problem *p, const double *b, double *x, cudaStream_t s) {
         const RowOp A = fine_op(p);
-        PK_FMT_SWITCH(p->spmv_tpr, (kg_residual<TPR><<<kRedGrid, kBlock, 0, s>>>(
+        PK_FMT_SWITCH(p->spmv_tpr, (kg_residual<TPR><<<fine_grid(p), kBlock, 0, s>>>(
                                        p->nh, A, b, x, p->gm_V, p->gm_state, p->gm_g, p->d_partials,
                                        p->d_counter, p->d_hist, 1)));
         PK_LAUNCH();
@@ -91,7 +91,7 @@ struct Gmres {
         const int64_t n = p->nh;
         const RowOp A = fine_op(p);
         apply_prec(p, p->gm_vin, p->gm_zout, s);
-        PK_FMT_SWITCH(p->spmv_tpr, (kg_spmv_w<TPR><<<kRedGrid, kBlock, 0, s>>>(n, A, p->gm_zout, p->gm_w, p->gm_Z,
+        PK_FMT_SWITCH(p->spmv_tpr, (kg_spmv_w<TPR><<<fine_grid(p), kBlock, 0, s>>>(n, A, p->gm_zout, p->gm_w, p->gm_Z,
                                                                               p->gm_state)));
         PK_LAUNCH();
         const dim3 dg(kDotChunks, p->gm_m + 1);
@@ -112,7 +112,7 @@ struct Gmres {
         PK_LAUNCH();
         kg_update_x<<<elem_blocks(n), kBlock, 0, s>>>(n, x, p->gm_Z, p->gm_y, p->gm_state);
         PK_LAUNCH();
-        PK_FMT_SWITCH(p->spmv_tpr, (kg_residual<TPR><<<kRedGrid, kBlock, 0, s>>>(
+        PK_FMT_SWITCH(p->spmv_tpr, (kg_residual<TPR><<<fine_grid(p), kBlock, 0, s>>>(
                                        n, A, b, x, p->gm_V, p->gm_state, p->gm_g, p->d_partials, p->d_counter,
                                        p->d_hist, 0)));
         PK_LAUNCH();

@@ -942,30 +942,34 @@ void apply_vcycle(pkasp_problem *p, const double *b, double *x, cudaStream_t s) 
 
 namespace {
 
+
 void enqueue_init(pkasp_problem *p, const double *b, double *x, cudaStream_t s) {
     const int tpr = p->spmv_tpr;
     const RowOp A = fine_op(p);
-    PK_FMT_SWITCH(tpr, (k_init_residual<TPR><<<kRedGrid, kBlock, 0, s>>>(
+    PK_FMT_SWITCH(tpr, (k_init_residual<TPR><<<fine_grid(p), kBlock, 0, s>>>(
                            p->nh, A, b, x, p->w_r, p->d_state, p->d_partials, p->d_counter, p->d_hist)));
     PK_LAUNCH();
     apply_prec(p, p->w_r, p->w_z, s);
-    k_start<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_r, p->w_z, p->w_p, p->d_state, p->d_partials, p->d_counter);
+    k_start<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_r, p->w_z, p->w_p, p->d_state, p->d_partials,
+                                              p->d_counter);
     PK_LAUNCH();
 }
+
 
 void enqueue_iteration(pkasp_problem *p, double *x, cudaStream_t s) {
     const int tpr = p->spmv_tpr;
     const RowOp A = fine_op(p);
-    PK_FMT_SWITCH(tpr, (k_spmv_pq<TPR><<<kRedGrid, kBlock, 0, s>>>(p->nh, A, p->w_p, p->w_q, p->d_state,
-                                                                   p->d_partials, p->d_counter)));
+    const unsigned fg = fine_grid(p);
+    PK_FMT_SWITCH(tpr, (k_spmv_pq<TPR><<<fg, kBlock, 0, s>>>(p->nh, A, p->w_p, p->w_q, p->d_state,
+                                                             p->d_partials, p->d_counter)));
     PK_LAUNCH();
     k_update_xr<<<kRedGrid, kBlock, 0, s>>>(p->nh, x, p->w_r, p->w_p, p->w_q, p->d_state, p->d_partials,
-                                            p->d_counter, p->d_hist);
+                                                  p->d_counter, p->d_hist);
     PK_LAUNCH();
     apply_prec(p, p->w_r, p->w_z, s);
     const int flex = (p->opt.flexible || p->opt.precond_precision == PKASP_PREC_FP32) ? 1 : 0;
     k_beta<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_r, p->w_z, p->w_q, flex, p->d_state, p->d_partials,
-                                       p->d_counter);
+                                             p->d_counter);
     PK_LAUNCH();
     k_update_p<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_z, p->w_p, p->d_state);
     PK_LAUNCH();
@@ -974,8 +978,8 @@ void enqueue_iteration(pkasp_problem *p, double *x, cudaStream_t s) {
 void enqueue_final(pkasp_problem *p, const double *b, const double *x, cudaStream_t s) {
     const int tpr = p->spmv_tpr;
     const RowOp A = fine_op(p);
-    PK_FMT_SWITCH(tpr, (k_true_residual<TPR><<<kRedGrid, kBlock, 0, s>>>(p->nh, A, b, x, p->d_state,
-                                                                         p->d_partials, p->d_counter)));
+    PK_FMT_SWITCH(tpr, (k_true_residual<TPR><<<fine_grid(p), kBlock, 0, s>>>(p->nh, A, b, x, p->d_state,
+                                                                             p->d_partials, p->d_counter)));
     PK_LAUNCH();
 }
 

@@ -167,7 +167,8 @@ void op(pkasp_problem *p, const double *x, double *y, const int *gate, cudaStrea
     const int64_t nh = S.nh, nu = 3 * nh;
     const RowOp A = fine_op(p);
     for (int c = 0; c < 3; ++c) {
-        PK_FMT_SWITCH(p->spmv_tpr, (ks_op_u<TPR><<<kRedGrid, kBlock, 0, s>>>(nh, A, x + c * nh, y + c * nh, gate)));
+        PK_FMT_SWITCH(p->spmv_tpr, (ks_op_u<TPR><<<fine_grid(p), kBlock, 0, s>>>(nh, A, x + c * nh, y + c * nh,
+                                                                                   gate)));
         PK_LAUNCH();
     }
     ks_add_csr<<<grid_for(nu), kBlock, 0, s>>>(nu, S.BT.ptr, S.BT.col, S.BT.val, x + nu, y, gate);
