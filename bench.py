@@ -383,7 +383,7 @@ def main():
     roof_spmv = {"bound": "hbm", "kernel": "k_spmv_pq / k_sell_spmv (fine SpMV, SELL-32, FP64)",
                  "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                  "frac_of_nominal_8000": achieved / NOMINAL_HBM_GBS,
-                 "traffic": 552.3e6 + 8.1e6 if p3 else None, "traffic_source":
+                 "traffic": 548.3e6 + 8.3e6 if p3 else None, "traffic_source":
                  "ncu dram__bytes_read+write of one k_spmv_pq launch, profiles/k_spmv_pq_sell_p3_n32.md"
                  if p3 else None,
                  "peak_source": src, "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms}
