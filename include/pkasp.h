@@ -351,6 +351,17 @@ int pkasp_dofmap_host(const double *xyz_host, int64_t nv, const int32_t *tets_ho
                       int64_t *ah_ptr_host, int32_t *ah_col_host, int64_t *pi_ptr_host,
                       int32_t *pi_col_host, double *pi_val_host);
 
+/* The Taylor-Hood P_k - P_{k-1} blocks of Sec. 5 on the host, as pkasp_stokes_setup
+ * assembles them (k = 2..4; mesh arguments as pkasp_assemble): sizes_out[4] = {n_h, n_p,
+ * nnz(B), nnz(M_p)}. B = -div_h is n_p x 3 n_h (rows: every P_{k-1} node; columns: the
+ * velocity unknowns component-major, c n_h + j), M_p the n_p x n_p pressure mass matrix;
+ * rows in CSR with ascending columns. Non-NULL arrays are filled: b_ptr[n_p+1],
+ * b_col/b_val[nnz(B)], m_ptr[n_p+1], m_col/m_val[nnz(M_p)]. Call once with NULL arrays
+ * to learn the sizes. Errors: EINVAL, EMESH. */
+int pkasp_stokes_blocks_host(const double *xyz_host, int64_t nv, const int32_t *tets_host, int64_t nt, int k,
+                             int64_t *sizes_out, int64_t *b_ptr, int32_t *b_col, double *b_val,
+                             int64_t *m_ptr, int32_t *m_col, double *m_val);
+
 /* Reference tensors S[a][b][m][n] = (1/|T|) int_T (d phi_m/d lambda_a)(d phi_n/d lambda_b)
  * of the degree-k Lagrange basis (S_out has 16 nloc^2 entries): the element matrix of
  * Eq. (7) is kappa |T| sum_ab (grad lambda_a . grad lambda_b) S[a][b]. Host only. */

@@ -86,6 +86,7 @@ SIGNATURES = [
     ("pkasp_pmis_noalloc", C.c_int, [i64, vp, vp, vp, C.c_uint64, vp, vp]),
     ("pkasp_dofmap_host", C.c_int, [vp, i64, vp, i64, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp]),
     ("pkasp_reference_tensors", C.c_int, [C.c_int, vp]),
+    ("pkasp_stokes_blocks_host", C.c_int, [vp, i64, vp, i64, C.c_int, vp, vp, vp, vp, vp, vp, vp]),
     ("pkasp_time_kernel", C.c_int, [vp, C.c_int, C.c_int, C.POINTER(C.c_float), vp]),
     ("pkasp_stokes_setup", C.c_int, [vp, C.c_int, vp]),
     ("pkasp_stokes_sizes", C.c_int, [vp, vp]),

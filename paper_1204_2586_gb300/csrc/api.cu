@@ -547,6 +547,35 @@ int pkasp_dofmap_host(const double *xyz_host, int64_t nv, const int32_t *tets_ho
     });
 }
 
+int pkasp_stokes_blocks_host(const double *xyz_host, int64_t nv, const int32_t *tets_host, int64_t nt, int k,
+                             int64_t *sizes_out, int64_t *b_ptr, int32_t *b_col, double *b_val,
+                             int64_t *m_ptr, int32_t *m_col, double *m_val) {
+    if (!xyz_host || !tets_host || !sizes_out) return set_error(PKASP_EINVAL, "NULL argument");
+    if (nv <= 0 || nt <= 0 || k < 2 || k > 4) return set_error(PKASP_EINVAL, "bad sizes or degree (k = 2..4)");
+    for (int64_t i = 0; i < 4 * nt; ++i)
+        if (tets_host[i] < 0 || tets_host[i] >= nv)
+            return set_error(PKASP_EMESH, "tetrahedron vertex index out of range");
+    return guarded([&]() -> int {
+        pk::DofMap D;
+        pk::HostMesh M{k, nv, nt, xyz_host, tets_host};
+        pk::build_dofmap(M, D);
+        pk::HCSR B, BT, Mp;
+        int64_t np = 0;
+        pk::stokes_blocks(k, nv, nt, xyz_host, tets_host, D.nh, D.elem_dof.data(), B, BT, Mp, np);
+        sizes_out[0] = D.nh;
+        sizes_out[1] = np;
+        sizes_out[2] = B.ptr.back();
+        sizes_out[3] = Mp.ptr.back();
+        if (b_ptr) memcpy(b_ptr, B.ptr.data(), sizeof(int64_t) * B.ptr.size());
+        if (b_col) memcpy(b_col, B.col.data(), sizeof(int32_t) * B.col.size());
+        if (b_val) memcpy(b_val, B.val.data(), sizeof(double) * B.val.size());
+        if (m_ptr) memcpy(m_ptr, Mp.ptr.data(), sizeof(int64_t) * Mp.ptr.size());
+        if (m_col) memcpy(m_col, Mp.col.data(), sizeof(int32_t) * Mp.col.size());
+        if (m_val) memcpy(m_val, Mp.val.data(), sizeof(double) * Mp.val.size());
+        return PKASP_OK;
+    });
+}
+
 int pkasp_reference_tensors(int k, double *S_out) {
     if (k < 1 || k > 4 || !S_out) return set_error(PKASP_EINVAL, "bad argument");
     return guarded([&]() -> int {

@@ -293,6 +293,9 @@ void free_gmres(pkasp_problem *p);
 // Stokes (stokes.cpp: host assembly of B = -div_h, B^T and the pressure mass matrix;
 // stokes.cu: operator, block preconditioner, FGMRES)
 void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t &np);
+// the same from a mesh and its P_k unknown map (elem_dof[nt][nloc(k)]), host only
+void stokes_blocks(int k, int64_t nv, int64_t nt, const double *xyz, const int32_t *tets, int64_t nh,
+                   const int32_t *elem_dof, HCSR &B, HCSR &BT, HCSR &M, int64_t &np);
 void stokes_setup(pkasp_problem *p, int mp_iters, cudaStream_t s);
 void stokes_free(pkasp_problem *p);
 void stokes_apply(pkasp_problem *p, const double *x, double *y, cudaStream_t s);

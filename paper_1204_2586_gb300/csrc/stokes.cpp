@@ -91,11 +91,11 @@ void node_incidence(int64_t nnodes, int64_t nt, int nl, const std::vector<int32_
 
 }  // namespace
 
-void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t &np) {
-    const int k = p->k, kp = k - 1;
+void stokes_blocks(int k, int64_t nv, int64_t nt, const double *xyz, const int32_t *tets, int64_t nh,
+                   const int32_t *elem_dof, HCSR &B, HCSR &BT, HCSR &M, int64_t &np) {
+    const int kp = k - 1;
     const int nu = nloc_of(k), npl = nloc_of(kp);
-    const int64_t nt = p->nt, nh = p->nh;
-    HostMesh hm{kp, p->nv, nt, p->xyz.data(), p->tets.data()};
+    HostMesh hm{kp, nv, nt, xyz, tets};
     DofMap Dp;
     build_dofmap(hm, Dp);
     np = Dp.n_all;
@@ -133,7 +133,7 @@ void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t
     for (int64_t t = 0; t < nt; ++t) {
         double X[12], g[4][3];
         for (int v = 0; v < 4; ++v)
-            for (int c = 0; c < 3; ++c) X[3 * v + c] = p->xyz[3 * (int64_t)p->tets[4 * t + v] + c];
+            for (int c = 0; c < 3; ++c) X[3 * v + c] = xyz[3 * (int64_t)tets[4 * t + v] + c];
         vols[t] = tet_gradients(X, g);
         for (int a = 0; a < 4; ++a)
             for (int c = 0; c < 3; ++c) grads[t * 12 + a * 3 + c] = g[a][c];
@@ -156,7 +156,7 @@ void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t
             for (int64_t x = iptr[q]; x < iptr[q + 1]; ++x) {
                 const int64_t t = ient[x] / 64;
                 for (int n = 0; n < nu; ++n) {
-                    const int32_t j = p->elem_dof[t * nu + n];
+                    const int32_t j = elem_dof[t * nu + n];
                     if (j < 0) continue;
                     for (int c = 0; c < 3; ++c) bc.push_back((int32_t)(c * nh + j));
                 }
@@ -190,7 +190,7 @@ void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t
                 const double vol = vols[t];
                 const double *g = &grads[t * 12];
                 for (int n = 0; n < nu; ++n) {
-                    const int32_t j = p->elem_dof[t * nu + n];
+                    const int32_t j = elem_dof[t * nu + n];
                     if (j < 0) continue;
                     for (int c = 0; c < 3; ++c) {
                         double s = 0.0;
@@ -223,6 +223,10 @@ void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t
             BT.col[o] = (int32_t)q;
             BT.val[o] = B.val[x];
         }
+}
+
+void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t &np) {
+    stokes_blocks(p->k, p->nv, p->nt, p->xyz.data(), p->tets.data(), p->nh, p->elem_dof.data(), B, BT, M, np);
 }
 
 }  // namespace pk

@@ -299,6 +299,29 @@ def dofmap_host(xyz, tets, k):
                 ah_ptr=ap, ah_col=ac[:nnz_h], pi_ptr=pp, pi_col=pc[:nnz_pi], pi_val=pv[:nnz_pi])
 
 
+def stokes_blocks_host(xyz, tets, k):
+    """Host-only Taylor-Hood blocks of the library (B = -div_h, M_p): dict with n_h, n_p and
+    CSR arrays b_ptr/b_col/b_val, m_ptr/m_col/m_val."""
+    lib = L.load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    nt = tets.shape[0]
+    sz = np.zeros(4, np.int64)
+    L.check(lib.pkasp_stokes_blocks_host(xyz.ctypes.data, xyz.shape[0], tets.ctypes.data, nt, k, sz.ctypes.data,
+                                         None, None, None, None, None, None))
+    nh, npr, nb, nm = (int(v) for v in sz)
+    out = dict(n_h=nh, n_p=npr, b_ptr=np.zeros(npr + 1, np.int64), b_col=np.zeros(max(nb, 1), np.int32),
+               b_val=np.zeros(max(nb, 1)), m_ptr=np.zeros(npr + 1, np.int64), m_col=np.zeros(max(nm, 1), np.int32),
+               m_val=np.zeros(max(nm, 1)))
+    L.check(lib.pkasp_stokes_blocks_host(xyz.ctypes.data, xyz.shape[0], tets.ctypes.data, nt, k, sz.ctypes.data,
+                                         out["b_ptr"].ctypes.data, out["b_col"].ctypes.data,
+                                         out["b_val"].ctypes.data, out["m_ptr"].ctypes.data,
+                                         out["m_col"].ctypes.data, out["m_val"].ctypes.data))
+    for key, m in (("b_col", nb), ("b_val", nb), ("m_col", nm), ("m_val", nm)):
+        out[key] = out[key][:m]
+    return out
+
+
 def reference_tensors(k):
     nl = (k + 1) * (k + 2) * (k + 3) // 6
     S = np.zeros((4, 4, nl, nl))

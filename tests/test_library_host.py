@@ -10,7 +10,7 @@ import pytest
 
 from paper_1204_2586_gb300 import _lib as L
 from paper_1204_2586_gb300 import build as B
-from paper_1204_2586_gb300.inputs import kuhn_mesh
+from paper_1204_2586_gb300.inputs import kappa_lognormal, kuhn_mesh
 from paper_1204_2586_gb300.solver import dofmap_host, reference_tensors
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -88,6 +88,28 @@ def test_reference_tensors_match_oracle(lib, oracle_mod, k):
     assert np.allclose(S, So, rtol=0, atol=1e-12 * np.abs(So).max())
 
 
+@pytest.mark.parametrize("k,n,ks", [(2, 3, None), (3, 2, 1), (4, 2, None)])
+def test_stokes_blocks_match_oracle(lib, oracle_mod, k, n, ks):
+    """The Taylor-Hood blocks the library assembles on the host (B = -div_h, M_p; Sec. 5)
+    against the oracle's: patterns bit-exact, values within 1e-12 of the largest entry.
+    (Independent routes: quadrature reference tensors and a pressure-node incidence in
+    the library; the oracle's own element integrals and assembly.)"""
+    from paper_1204_2586_gb300.solver import stokes_blocks_host
+
+    xyz, t = kuhn_mesh(n, 0.2, 0)
+    kap = None if ks is None else kappa_lognormal(t.shape[0], ks)
+    S = stokes_blocks_host(xyz, t, k)
+    Ou = oracle_mod.Problem(xyz, t, k, kap)
+    Ou.setup()
+    Op = oracle_mod.Problem(xyz, t, k - 1, dirichlet=False)
+    OS = oracle_mod.Stokes(Ou, Op, 10)
+    assert (S["n_h"], S["n_p"]) == (OS.nh, OS.np)
+    for pre, which in (("b", 0), ("m", 2)):
+        o = OS.matrix(which)
+        assert np.array_equal(S[pre + "_ptr"], o.ptr) and np.array_equal(S[pre + "_col"], o.col)
+        assert np.abs(S[pre + "_val"] - o.val).max() <= 1e-12 * np.abs(o.val).max()
+
+
 def test_host_argument_errors(lib):
     xyz, t = kuhn_mesh(2, 0.2, 0)
     sz = np.zeros(6, np.int64)
@@ -110,6 +132,15 @@ def test_host_argument_errors(lib):
     assert rc == L.PKASP_EINVAL
     rc = lib.pkasp_solve(None, None, None, 1, 1, None, None)
     assert rc == L.PKASP_EINVAL
+    rc = lib.pkasp_solve_from_zero(None, None, None, 1, 1, None, None)
+    assert rc == L.PKASP_EINVAL
+    s4 = np.zeros(4, np.int64)
+    rc = lib.pkasp_stokes_blocks_host(xyz.ctypes.data, xyz.shape[0], t.ctypes.data, t.shape[0], 1, s4.ctypes.data,
+                                      None, None, None, None, None, None)
+    assert rc == L.PKASP_EINVAL  # Taylor-Hood needs k >= 2
+    rc = lib.pkasp_stokes_blocks_host(xyz.ctypes.data, xyz.shape[0], bad.ctypes.data, t.shape[0], 2,
+                                      s4.ctypes.data, None, None, None, None, None, None)
+    assert rc == L.PKASP_EMESH
 
 
 def test_no_cpu_fallback_in_package():
