@@ -61,6 +61,10 @@ def lib():
     L.orc_problem_dofs.argtypes = [vp, i64p, f64p]
     L.orc_problem_elem_dofs.argtypes = [vp, i32p]
     L.orc_set_kappa.argtypes = [vp, f64p]
+    L.orc_set_source_nodal.restype = C.c_int
+    L.orc_set_source_nodal.argtypes = [vp, f64p]
+    L.orc_problem_nodes.restype = None
+    L.orc_problem_nodes.argtypes = [vp, f64p]
     L.orc_csr_info.argtypes = [vp, i64p]
     L.orc_csr_copy.argtypes = [vp, i64p, i32p, f64p]
     L.orc_csr_free.argtypes = [vp]
@@ -359,6 +363,19 @@ class Problem:
     def set_kappa(self, kappa):
         lib().orc_set_kappa(self.h, _f64(kappa))
         self.opts = None
+
+    def nodes(self):
+        """Coordinates [n_all, 3] of every P_k node in the all-node numbering."""
+        x = np.zeros((self.nall, 3))
+        lib().orc_problem_nodes(self.h, x)
+        return x
+
+    def set_source_nodal(self, f_all):
+        """Load from a caller's f given at all n_all P_k nodes (its nodal interpolant)."""
+        f = _f64(f_all)
+        if f.shape != (self.nall,):
+            raise ValueError("f_all must hold one value per P_k node (n_all)")
+        lib().orc_set_source_nodal(self.h, f)
 
     def setup(self, **kw):
         o = default_opts(**kw)

@@ -64,6 +64,7 @@ struct oproblem {
     int32_t *inc_tet, *inc_loc;
     ocsr *Ah, *AH, *Pi, *PiT;
     double *b;
+    double *f_all;    /* source 2: f at every P_k node (all-node numbering), else NULL */
     /* setup */
     int have_setup;
     oopts o;
@@ -758,6 +759,12 @@ static void assemble_values(oproblem *P) {
     free(K);
 }
 
+/* Load vector f_i = <f, phi_i> of Eq. (7) by the Grundmann-Moeller rule of degree
+ * 2k+3. source 1: the manufactured f, evaluated at the quadrature points; source 2: a
+ * caller's f given by its values at the P_k nodes, i.e. f_h = sum_n f_n phi_n (the
+ * nodal interpolant, Sec. 2), evaluated at the quadrature points through the basis.
+ * The rule is exact for f_h phi_i (degree 2k), so source 2 gives b = M f exactly up to
+ * rounding, M the P_k mass matrix. */
 static void assemble_load(oproblem *P) {
     int nl = P->nloc, s = P->k + 1;
     double lam[4 * 512], w[512];
@@ -772,6 +779,12 @@ static void assemble_load(oproblem *P) {
         double vol = tet_geom(x12, G);
         double fq[512];
         for (int q = 0; q < nq; ++q) {
+            if (P->source == 2) {
+                double v = 0.0;
+                for (int n = 0; n < nl; ++n) v += P->f_all[P->elem_all[t * nl + n]] * phiq[q * nl + n];
+                fq[q] = v;
+                continue;
+            }
             double x[3];
             for (int c = 0; c < 3; ++c) {
                 double v = 0.0;
@@ -864,6 +877,31 @@ oproblem *orc_problem_create(int64_t nv, const double *xyz, int64_t nt, const in
     return P;
 }
 
+/* Replaces the source by a caller's f at all P_k nodes (f_all[n_all], all-node
+ * numbering of the DOF map, boundary nodes included) and re-assembles the load. */
+int orc_set_source_nodal(oproblem *P, const double *f_all) {
+    if (!P->f_all) P->f_all = (double *)xmalloc(sizeof(double) * (size_t)P->nall);
+    memcpy(P->f_all, f_all, sizeof(double) * (size_t)P->nall);
+    P->source = 2;
+    assemble_load(P);
+    return 0;
+}
+
+/* Coordinates of all n_all P_k nodes (x = sum_a m_a v_a / k over any element holding
+ * the node), in the all-node numbering. */
+void orc_problem_nodes(const oproblem *P, double *xyz_all) {
+    int nl = P->nloc;
+    for (int64_t t = 0; t < P->nt; ++t)
+        for (int m = 0; m < nl; ++m) {
+            int64_t d = P->elem_all[t * nl + m];
+            for (int c = 0; c < 3; ++c) {
+                double v = 0.0;
+                for (int a = 0; a < 4; ++a) v += (double)P->mi[m][a] * P->xyz[3 * (int64_t)P->tets[4 * t + a] + c];
+                xyz_all[3 * d + c] = v / (double)P->k;
+            }
+        }
+}
+
 int orc_set_kappa(oproblem *P, const double *kappa) {
     for (int64_t t = 0; t < P->nt; ++t) P->kappa[t] = kappa[t];
     assemble_values(P);
@@ -902,6 +940,7 @@ void orc_problem_free(oproblem *P) {
     free(P->mi);
     free(P->S);
     free(P->elem_all);
+    free(P->f_all);
     free(P->elem_dof);
     free(P->elem_vdof);
     free(P->dof_all);

@@ -44,6 +44,8 @@ void orc_problem_rhs(const oproblem *p, double *b);
 void orc_problem_dofs(const oproblem *p, int64_t *dof_all, double *dof_xyz);
 void orc_problem_elem_dofs(const oproblem *p, int32_t *elem_dof);
 int orc_set_kappa(oproblem *p, const double *kappa);
+int orc_set_source_nodal(oproblem *p, const double *f_all);
+void orc_problem_nodes(const oproblem *p, double *xyz_all);
 
 /* CSR access */
 void orc_csr_info(const ocsr *a, int64_t *out3);

@@ -192,6 +192,54 @@ def test_kuhn_sizes_match_closed_form(oracle_mod):
         assert P.nall == (k * n + 1) ** 3
 
 
+def _monomial(p):
+    return lambda X: X[:, 0] ** p[0] * X[:, 1] ** p[1] * X[:, 2] ** p[2]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_nodal_load_integrates_products_exactly(oracle_mod, k):
+    """Load from a caller's f given at the P_k nodes: b_i = <f_h, phi_i> with f_h the
+    nodal interpolant (Sec. 2). Without Dirichlet removal every node is an unknown, and
+    for polynomials f, g of degree <= k the interpolants are exact, so
+    b(f) . g(nodes) = int_{[0,1]^3} f g = prod_c 1 / (a_c + d_c + 1) for monomials
+    x^a, x^d (a closed form; the jittered mesh still tiles the unit cube exactly). A
+    wrong quadrature weight, basis function or node index changes these integrals."""
+    xyz, t = _mesh(3, seed=5)
+    O = oracle_mod.Problem(xyz, t, k, source=oracle_mod.SOURCE_NONE, dirichlet=False)
+    X = O.nodes()
+    dof_all, dx = O.dofs()
+    assert O.nh == O.nall
+    assert np.array_equal(X[dof_all], dx)
+    exps = [p for p in itertools.product(range(k + 1), repeat=3) if sum(p) <= k]
+    rng = np.random.default_rng(k)
+    picks = [exps[i] for i in rng.choice(len(exps), size=min(6, len(exps)), replace=False)]
+    for a in picks:
+        O.set_source_nodal(_monomial(a)(X))
+        b = O.rhs()
+        for d in picks:
+            want = np.prod([1.0 / (a[c] + d[c] + 1) for c in range(3)])
+            got = b @ _monomial(d)(X[dof_all])
+            assert abs(got - want) <= 1e-13 * max(1.0, abs(want)), (a, d, got, want)
+
+
+def test_nodal_load_of_the_sine_interpolant_converges(oracle_mod):
+    """With Dirichlet removal, the load of the nodal interpolant of the manufactured f
+    approaches the quadrature load of f itself at the interpolation order: the
+    difference b_nodal - b_sine integrates (I_k f - f) phi_i, so its size relative to b
+    falls by about 2^{k+1} when h halves (k = 2: ratio >= 6)."""
+    errs = []
+    for n in (4, 8):
+        xyz, t = kuhn_mesh(n, 0.2, 0)
+        O = oracle_mod.Problem(xyz, t, 2)
+        b_sine = O.rhs()
+        X = O.nodes()
+        O.set_source_nodal(3 * np.pi ** 2 * np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) *
+                           np.sin(np.pi * X[:, 2]))
+        b_nod = O.rhs()
+        errs.append(np.abs(b_nod - b_sine).max() / np.abs(b_sine).max())
+    assert errs[0] / errs[1] >= 6.0, errs
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("k", [2, 3, 4])
 def test_manufactured_solution_rate(oracle_mod, k):
@@ -376,6 +424,109 @@ def test_extpi_preserves_constants_and_pattern(oracle_mod):
     for i in np.nonzero(cf == 1)[0]:
         assert list(Ps.indices[Ps.indptr[i]:Ps.indptr[i + 1]]) == [cidx[i]]
         assert Ps.data[Ps.indptr[i]] == 1.0
+
+
+def _entries_csr(oracle_mod, n, entries):
+    """CSR matrix of n rows from {(i, j): a_ij} (only the listed entries are stored),
+    with strong flags from the set of (i, j) pairs marked strong."""
+    rows = [[] for _ in range(n)]
+    for (i, j), v in entries.items():
+        rows[i].append((j, v))
+    ptr, col, val = [0], [], []
+    for r in rows:
+        r.sort()
+        col += [j for j, _ in r]
+        val += [v for _, v in r]
+        ptr.append(len(col))
+    return oracle_mod.CSR(np.array(ptr, np.int64), np.array(col, np.int32), np.array(val), (n, n))
+
+
+def _extpi_rows(oracle_mod, n, entries, strong_pairs, cf, cc=0):
+    A = _entries_csr(oracle_mod, n, entries)
+    s = np.array([1 if (i, int(A.col[e])) in strong_pairs else 0
+                  for i in range(n) for e in range(A.ptr[i], A.ptr[i + 1])], np.uint8)
+    P = oracle_mod.extpi(A, s, np.array(cf, np.int8), cc=cc)
+    return {i: dict(zip(P.col[P.ptr[i]:P.ptr[i + 1]].tolist(), P.val[P.ptr[i]:P.ptr[i + 1]].tolist()))
+            for i in range(n)}
+
+
+def test_extpi_hand_weights_1d_cffc(oracle_mod):
+    """Extended+i weights computed by hand on the 1D Laplacian tridiag(-1, 2, -1) with the
+    splitting C F F C (every off-diagonal strong). For F point 1: C_1^s = {0}, F_1^s = {2},
+    C_2^s = {3}, so Chat_1 = {0, 3}; abar_2l = a_2l (all negative, a_22 > 0);
+    d_2 = abar_21 + abar_23 = -2; atil_11 = 2 + (-1)(-1)/(-2) = 3/2;
+    w_10 = -(-1 + 0)/(3/2) = 2/3, w_13 = -(0 + (-1)(-1)/(-2))/(3/2) = 1/3: the linear
+    interpolant between the two C points, as the distance-two reach of ext+i promises.
+    Point 2 mirrors it (1/3, 2/3). C points inject."""
+    e = {(0, 0): 2.0, (0, 1): -1.0, (1, 0): -1.0, (1, 1): 2.0, (1, 2): -1.0,
+         (2, 1): -1.0, (2, 2): 2.0, (2, 3): -1.0, (3, 2): -1.0, (3, 3): 2.0}
+    strong = {p for p in e if p[0] != p[1]}
+    P = _extpi_rows(oracle_mod, 4, e, strong, [1, -1, -1, 1])
+    assert P[0] == {0: 1.0} and P[3] == {1: 1.0}
+    assert P[1].keys() == {0, 1} and P[2].keys() == {0, 1}
+    assert abs(P[1][0] - 2 / 3) <= 1e-15 and abs(P[1][1] - 1 / 3) <= 1e-15
+    assert abs(P[2][0] - 1 / 3) <= 1e-15 and abs(P[2][1] - 2 / 3) <= 1e-15
+
+
+def test_extpi_hand_weights_sign_filter(oracle_mod):
+    """The abar filter of extended+i: a connection a_kl of an F neighbour k whose sign
+    equals that of a_kk is dropped. Points: 0 F, 1 F, 2 C, 3 C; row 0: a_00 = 4,
+    a_01 = -2 (strong F), a_02 = -1 (strong C); row 1: a_11 = 5, a_10 = -2 (strong),
+    a_12 = +1 (positive, weak), a_13 = -2 (strong C). Chat_0 = {2} u C_1^s = {2, 3}.
+    abar_10 = -2, abar_12 = 0 (filtered), abar_13 = -2, so d_1 = 0 - 2 - 2 = -4;
+    atil_00 = 4 + (-2)(-2)/(-4) = 3; w_02 = -(-1 + 0)/3 = 1/3;
+    w_03 = -(0 + (-2)(-2)/(-4))/3 = 1/3. Without the filter the weights would be 1/8
+    and 1/2."""
+    e = {(0, 0): 4.0, (0, 1): -2.0, (0, 2): -1.0,
+         (1, 0): -2.0, (1, 1): 5.0, (1, 2): 1.0, (1, 3): -2.0,
+         (2, 0): -1.0, (2, 1): 1.0, (2, 2): 3.0, (3, 1): -2.0, (3, 3): 3.0}
+    strong = {(0, 1), (0, 2), (1, 0), (1, 3), (2, 0), (3, 1)}
+    P = _extpi_rows(oracle_mod, 4, e, strong, [-1, -1, 1, 1])
+    assert P[0].keys() == {0, 1}
+    assert abs(P[0][0] - 1 / 3) <= 1e-15 and abs(P[0][1] - 1 / 3) <= 1e-15
+    # F point 1: C_1^s = {3}, F_1^s = {0}, C_0^s = {2}: Chat_1 = {2, 3};
+    # abar_0l: abar_01 = -2, abar_02 = -1, d_0 = abar_01 + abar_02 = -3;
+    # atil_11 = 5 + (-2)(-2)/(-3) = 11/3; the weak a_12 = +1 is in Chat_1, so
+    # w_12 = -(1 + (-2)(-1)/(-3))/(11/3) = -(1/3)/(11/3) = -1/11;
+    # w_13 = -(-2 + 0)/(11/3) = 6/11
+    assert P[1].keys() == {0, 1}
+    assert abs(P[1][0] + 1 / 11) <= 1e-15 and abs(P[1][1] - 6 / 11) <= 1e-15
+
+
+def test_extpi_hand_weights_zero_denominator_lumped(oracle_mod):
+    """A strong F neighbour k whose denominator d_k = sum over Chat_i u {i} of abar_kl
+    is zero is lumped into the diagonal: atil_ii += a_ik. Points: 0 F, 1 F, 2 C, 3 F;
+    row 0: a_00 = 4, a_01 = -2 (strong F), a_02 = -1 (strong C); row 1: a_11 = 3,
+    a_10 = +1 (filtered: same sign as a_11), a_13 = -1 (an F point outside Chat_0).
+    Chat_0 = {2} (k = 1 has no strong C point), d_1 = abar_10 + abar_12 = 0 + 0 = 0,
+    atil_00 = 4 + (-2) = 2, w_02 = -(-1)/2 = 1/2 (dropping k instead would give 1/4).
+    Point 3 has no strong C point within distance two: an empty row."""
+    e = {(0, 0): 4.0, (0, 1): -2.0, (0, 2): -1.0,
+         (1, 0): 1.0, (1, 1): 3.0, (1, 3): -1.0,
+         (2, 0): -1.0, (2, 2): 2.0, (3, 1): -1.0, (3, 3): 2.0}
+    strong = {(0, 1), (0, 2), (1, 3), (2, 0), (3, 1)}
+    P = _extpi_rows(oracle_mod, 4, e, strong, [-1, -1, 1, -1])
+    assert P[0] == {0: 0.5}
+    assert P[3] == {}
+
+
+def test_extpi_cc_hand_weights(oracle_mod):
+    """The "+cc" rule by hand: points 0 F, 1 F, 2 C, 3 C; row 0: a_00 = 4, a_01 = -1,
+    a_02 = -2; row 1: a_11 = 4, a_10 = -1, a_12 = -1, a_13 = -2; all strong. F neighbour
+    1 shares the strong C point 2 with 0, so under +cc it adds nothing: Chat_0 = {2},
+    d_1 = abar_10 + abar_12 = -2, atil_00 = 4 + (-1)(-1)/(-2) = 7/2,
+    w_02 = -(-2 + (-1)(-1)/(-2))/(7/2) = 5/7. Plain extended+i takes Chat_0 = {2, 3},
+    d_1 = -4, atil_00 = 15/4, w_02 = 3/5, w_03 = 2/15."""
+    e = {(0, 0): 4.0, (0, 1): -1.0, (0, 2): -2.0,
+         (1, 0): -1.0, (1, 1): 4.0, (1, 2): -1.0, (1, 3): -2.0,
+         (2, 0): -2.0, (2, 1): -1.0, (2, 2): 4.0, (3, 1): -2.0, (3, 3): 4.0}
+    strong = {p for p in e if p[0] != p[1]}
+    cf = [-1, -1, 1, 1]
+    Pc = _extpi_rows(oracle_mod, 4, e, strong, cf, cc=1)
+    assert Pc[0].keys() == {0} and abs(Pc[0][0] - 5 / 7) <= 1e-15
+    P0 = _extpi_rows(oracle_mod, 4, e, strong, cf, cc=0)
+    assert P0[0].keys() == {0, 1}
+    assert abs(P0[0][0] - 3 / 5) <= 1e-15 and abs(P0[0][1] - 2 / 15) <= 1e-15
 
 
 @pytest.mark.parametrize("theta", [0.25, 0.5])
