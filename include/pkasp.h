@@ -53,7 +53,7 @@ enum { PKASP_MODE_ADDITIVE = 0, PKASP_MODE_MULTIPLICATIVE = 1, PKASP_MODE_AMG = 
 enum { PKASP_SMOOTHER_SGS = 0, PKASP_SMOOTHER_L1JACOBI = 1 };
 enum { PKASP_PREC_FP64 = 0, PKASP_PREC_FP32 = 1 };
 enum { PKASP_KRYLOV_CG = 0, PKASP_KRYLOV_FGMRES = 1 };
-enum { PKASP_SOURCE_NONE = 0, PKASP_SOURCE_SINE = 1 };
+enum { PKASP_SOURCE_NONE = 0, PKASP_SOURCE_SINE = 1, PKASP_SOURCE_NODAL = 2 };
 enum { PKASP_MAX_LEVELS = 25, PKASP_MAX_COLS = 64 };
 
 /* Solver options (pkasp_default_options fills the defaults given in brackets). */
@@ -159,43 +159,60 @@ typedef struct {
  * Construction
  * ---------------------------------------------------------------------------------- */
 
-/* Fills *opt with the defaults listed in pkasp_options. */
+/* Fills *opt with the defaults listed in pkasp_options (the settings of Sec. 6.1-6.2
+ * where the paper gives them: theta, one pre- and one post-smoothing sweep). */
 void pkasp_default_options(pkasp_options *opt);
 
-/* Message of the last failed call on this thread (always NUL-terminated). */
+/* Message of the last failed call on this thread (always NUL-terminated); library
+ * plumbing with no counterpart in the paper. */
 int pkasp_last_error(char *buf, size_t n);
 
-/* Builds the P_k problem of Eq. (7) on a conforming tetrahedral mesh.
+/* Builds the P_k problem of Eq. (7) on a conforming tetrahedral mesh: the model problem
+ * -div(kappa grad u) = f of Eq. (1) (Sec. 2) in the Lagrange space V_h.
  *   xyz_host   [nv][3] vertex coordinates
  *   tets_host  [nt][4] vertex indices, positively oriented (det > 0)
  *   k          polynomial degree, 1..4 (the paper's V_h = P^{k,0}, Sec. 2)
  *   kappa      [nt] piecewise-constant coefficient, > 0 (host or device)
- *   source     PKASP_SOURCE_SINE: load f_i = <f, phi_i> for f = 3 pi^2 sin(pi x)
- *              sin(pi y) sin(pi z) by a degree 2k+3 Grundmann-Moeller rule;
+ *   source     the load f_i = <f, phi_i> of Eq. (7), by a degree 2k+3 Grundmann-Moeller
+ *              rule on every element:
+ *              PKASP_SOURCE_SINE: f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z);
+ *              PKASP_SOURCE_NODAL: the caller's f, given by f_nodal;
  *              PKASP_SOURCE_NONE: zero load (the caller passes its own b to solve).
+ *   f_nodal    PKASP_SOURCE_NODAL only (else NULL): [n_all] values of f at every P_k node,
+ *              boundary nodes included, in the node numbering below (host or device;
+ *              pkasp_nodes_host gives n_all and the node coordinates before assembly).
+ *              f is taken as its nodal interpolant f_h = sum_n f_n phi_n, so the load is
+ *              b = M f_nodal exactly up to rounding (M the P_k mass matrix; the rule is
+ *              exact for f_h phi_i). The library keeps a copy (pkasp_set_kappa reuses it).
  * Dirichlet nodes (those on faces with one adjacent element) are removed (Eq. 1,
- * u = 0 on the boundary). The DOF numbering is: vertices, then edges sorted by vertex
+ * u = 0 on the boundary). The node numbering is: vertices, then edges sorted by vertex
  * pair (nodes from the lower vertex), then faces sorted by vertex triple (nodes in
  * ascending multi-index order), then element interiors; unknowns keep that order.
  * Assembles A_h (Eq. 7), the P1 matrix A_H of the same mesh and Pi = I_P (Eq. 10) on
- * the device. Errors: EINVAL, EMESH (det <= 0, index out of range), ENOMEM, ECUDA.
- * On success *out owns everything; release it with pkasp_destroy. */
+ * the device. Errors: EINVAL (sizes, degree, source, f_nodal given without
+ * PKASP_SOURCE_NODAL or missing with it), EMESH (det <= 0, index out of range), ENOMEM,
+ * ECUDA. On success *out owns everything; release it with pkasp_destroy. */
 int pkasp_assemble(const double *xyz_host, int64_t nv, const int32_t *tets_host, int64_t nt,
-                   int k, const double *kappa, int source, pkasp_problem **out);
+                   int k, const double *kappa, int source, const double *f_nodal,
+                   pkasp_problem **out);
 
-/* Sizes and setup statistics (host struct). */
+/* Sizes and setup statistics (host struct): n_h = dim V_h with the Dirichlet nodes
+ * removed (Sec. 2), n_H = dim of the P1 space V_H, the AMG levels of B_1 (Sec. 6.1) and
+ * the operator complexity of Sec. 6.2 / Table 6. No GPU work. */
 int pkasp_problem_info(const pkasp_problem *p, pkasp_info *info);
 
-/* Numbering of the unknowns: dof_all_host[n_h] = index among all P_k nodes (the
- * convention of pkasp_assemble) and dof_xyz_host[n_h][3] = node coordinates. Either may
- * be NULL. */
+/* Numbering of the unknowns (the nodes x_i^h of V_h, Sec. 2): dof_all_host[n_h] = index
+ * among all P_k nodes (the convention of pkasp_assemble) and dof_xyz_host[n_h][3] = node
+ * coordinates. Either may be NULL. Host copies; no GPU work. */
 int pkasp_get_dofmap(const pkasp_problem *p, int64_t *dof_all_host, double *dof_xyz_host);
 
-/* Copies the assembled load vector f_h (Eq. 7) into b[n_h] (host or device). */
+/* Copies the assembled load vector f_h (Eq. 7) into b[n_h] (host or device).
+ * Synchronises the stream. */
 int pkasp_get_rhs(const pkasp_problem *p, double *b, pkasp_stream_t stream);
 
-/* Replaces kappa [nt] (host or device, > 0) and re-assembles A_h, A_H and f_h on the
- * same sparsity pattern. Invalidates the setup (call pkasp_setup again). */
+/* Replaces the coefficient kappa of Eq. (1) [nt] (host or device, > 0) and re-assembles
+ * A_h, A_H (Eq. 7) and f_h on the same sparsity pattern, with the source given to
+ * pkasp_assemble. Invalidates the setup (call pkasp_setup again). Synchronises. */
 int pkasp_set_kappa(pkasp_problem *p, const double *kappa, pkasp_stream_t stream);
 
 /* Builds the preconditioner on the device: Jones-Plassmann colouring of A_h, strength
@@ -210,8 +227,10 @@ int pkasp_setup(pkasp_problem *p, const pkasp_options *opt, pkasp_stream_t strea
  * Solve
  * ---------------------------------------------------------------------------------- */
 
-/* Preconditioned CG on A_h x = b for ncols right-hand sides (1..64), columns
- * independent (each converges, stops and is reported on its own). b and x are
+/* Preconditioned CG on A_h x = b (Eq. 7) with the auxiliary-space preconditioner
+ * B = S_k + Pi B_1 Pi^T of Sec. 2 (or the form chosen at setup), for ncols right-hand
+ * sides (1..64), columns independent (each converges, stops and is reported on its
+ * own). With the FP32 preconditioner the outer iteration is flexible CG. b and x are
  * [n_h][ld] (host or device); x holds the initial guess on entry and the solution on
  * exit. Stops when ||r_k|| <= tol ||r_0|| per column, then checks the true residual and
  * restarts once if it is above tol. Fills *st (may be NULL) and synchronises the stream.
@@ -226,19 +245,23 @@ int pkasp_solve(pkasp_problem *p, const double *b, double *x, int ncols, int64_t
 int pkasp_solve_from_zero(pkasp_problem *p, const double *b, double *x, int ncols, int64_t ld,
                           pkasp_stats *st, pkasp_stream_t stream);
 
-/* Adjoint solve A_h^T lambda = g (A_h is symmetric, so this is the same operator and
- * preconditioner): lambda holds the initial guess on entry. Same conventions as
- * pkasp_solve. */
+/* Adjoint solve A_h^T lambda = g for the gradient of a loss L(u) of the solution of
+ * Eq. (7) (g = dL/du; the paper has no adjoint, this is the discrete adjoint of its
+ * system). A_h is symmetric, so this is the same operator and preconditioner: lambda
+ * holds the initial guess on entry. Same conventions and errors as pkasp_solve. */
 int pkasp_solve_adjoint(pkasp_problem *p, const double *g, double *lambda, int ncols,
                         int64_t ld, pkasp_stats *st, pkasp_stream_t stream);
 
-/* Element-wise gradient dL/dkappa_e = -lambda_e^T Khat_e u_e, Khat_e the element matrix
- * of Eq. (7) with kappa_e = 1 (A_h is linear in kappa_e), for u, lambda [n_h] (device)
- * and dkappa_dev [nt]. */
+/* Element-wise gradient dL/dkappa_e = -sum_c lambda_{c,e}^T Khat_e u_{c,e}, Khat_e the
+ * element matrix of Eq. (7) with kappa_e = 1 (A_h is linear in kappa_e), summed on the
+ * device over the ncols (1..64) columns of u and lambda ([n_h][ld] device arrays, column
+ * c at offset c, ld >= ncols): the gradient of a loss over a block of solves with one
+ * kappa. dkappa_dev [nt] (device) is overwritten. Enqueued on stream. Errors: EINVAL. */
 int pkasp_grad_kappa(const pkasp_problem *p, const double *u_dev, const double *lambda_dev,
-                     double *dkappa_dev, pkasp_stream_t stream);
+                     int ncols, int64_t ld, double *dkappa_dev, pkasp_stream_t stream);
 
-/* Frees the problem and all its device memory. NULL is accepted. */
+/* Frees the problem and all its device memory (synchronises the device first). NULL
+ * is accepted. */
 int pkasp_destroy(pkasp_problem *p);
 
 /* ------------------------------------------------------------------------------------
@@ -246,22 +269,27 @@ int pkasp_destroy(pkasp_problem *p);
  * All vectors are device memory of n_h (or n_H) entries.
  * ---------------------------------------------------------------------------------- */
 
-/* y = A_h x (Eq. 7). */
+/* y = A_h x (Eq. 7). Enqueued on stream. */
 int pkasp_spmv(const pkasp_problem *p, const double *x_dev, double *y_dev, pkasp_stream_t stream);
 
-/* z = B r with the preconditioner of the last pkasp_setup (FP64 or FP32 arithmetic). */
+/* z = B r with the preconditioner of the last pkasp_setup: additive B = S_k + Pi B_1
+ * Pi^T (Sec. 2), multiplicative (Algorithm 2.1 with Remark 2.1) or plain AMG on A_h
+ * (Sec. 6.2), in FP64 or FP32 arithmetic. Enqueued on stream; ESTATE before setup. */
 int pkasp_apply_prec(pkasp_problem *p, const double *r_dev, double *z_dev, pkasp_stream_t stream);
 
-/* z = S_k r from a zero guess (the P_k smoother alone). */
+/* z = S_k r from a zero guess: the P_k smoother of Sec. 2 alone (one forward and one
+ * backward multicolour Gauss-Seidel sweep, Remark 6.1, or l1-Jacobi). Enqueued. */
 int pkasp_apply_smoother(pkasp_problem *p, const double *r_dev, double *z_dev,
                          pkasp_stream_t stream);
 
-/* x = V(b): one AMG V(1,1)-cycle on A_H (b, x of n_H entries). */
+/* x = V(b): one AMG V(1,1)-cycle on A_H, the B_1 of Sec. 2 built as in Sec. 6.1
+ * (b, x of n_H entries). Enqueued on stream. */
 int pkasp_apply_vcycle(pkasp_problem *p, const double *b_dev, double *x_dev,
                        pkasp_stream_t stream);
 
 /* Copies matrix `which` to host CSR arrays (any may be NULL); *nnz_out (may be NULL)
- * receives the entry count. which: 0 A_h, 1 A_H, 2 Pi, 3 + 2l AMG level l matrix A_l,
+ * receives the entry count. which: 0 A_h (Eq. 7), 1 A_H, 2 Pi (Eq. 10), 3 + 2l AMG
+ * level l matrix A_l (Galerkin, Sec. 2 and 6.1),
  * 4 + 2l the interpolation P_l of level l; after pkasp_stokes_setup -1 B, -2 B^T,
  * -3 M_p. Synchronises. ptr is [rows+1]. */
 int pkasp_get_matrix(const pkasp_problem *p, int which, int64_t *rows_out, int64_t *cols_out,
@@ -301,12 +329,14 @@ int pkasp_stokes_apply_prec(pkasp_problem *p, const double *r_dev, double *z_dev
 int pkasp_stokes_solve(pkasp_problem *p, const double *b_dev, double *x_dev, pkasp_stats *st,
                        pkasp_stream_t stream);
 
-/* Colouring (colour per row) of A_h (level = -1) or of AMG level l; returns the count in
- * *ncolours (may be NULL). */
+/* Colouring (colour per row) of A_h (level = -1) or of AMG level l: the multicolour
+ * order of the Gauss-Seidel smoothers that replace the hybrid GS of Sec. 6.1; returns
+ * the count in *ncolours (may be NULL). Host output; synchronises. */
 int pkasp_get_colours(const pkasp_problem *p, int level, int32_t *colour_host, int *ncolours);
 
-/* C/F splitting (+1 C, -1 F) and strength flags (one byte per entry of A_l) of AMG
- * level l (not the coarsest). Either may be NULL. */
+/* C/F splitting (+1 C, -1 F; PMIS, Sec. 6.1) and strength flags (Sec. 6.2; one byte
+ * per entry of A_l) of AMG level l (not the coarsest). Either may be NULL. Host output;
+ * synchronises. */
 int pkasp_get_splitting(const pkasp_problem *p, int level, int8_t *cf_host, uint8_t *strong_host);
 
 /* PMIS on a caller-supplied strength graph (De Sterck, Yang & Heys 2006, cited in Sec. 1
@@ -324,11 +354,14 @@ int pkasp_pmis(int64_t n, const int64_t *ptr_dev, const int32_t *col_dev,
  * scratch is one fixed device array of about 17 MB inside the library, held by every GPU
  * that loads the library until the process exits, and it accepts at most
  * PKASP_NOALLOC_MAX_ROWS rows and PKASP_NOALLOC_MAX_NNZ entries (larger inputs return
- * PKASP_EINVAL before any work). The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress), so make the first call on each device before any stream
- * capture. Every call shares the one array: calls that overlap on the GPU (from several
- * streams or threads) race and must be serialized by the caller. The output cf_dev[n] is
- * bit-identical to pkasp_pmis for the same inputs. Synchronizes the stream. */
+ * PKASP_EINVAL before any kernel runs; so do row pointers that do not start at 0 or that
+ * decrease, columns outside [0, n), and patterns that are not structurally symmetric
+ * with ascending columns). Each call looks up that array's device address on the current
+ * device (cudaGetSymbolAddress). Every call shares the one array: calls that overlap on
+ * the GPU (from several streams or threads) race and must be serialized by the caller.
+ * The output cf_dev[n] is bit-identical to pkasp_pmis for the same inputs (both use the
+ * same per-row rules). It synchronizes the stream after every PMIS round (the host reads
+ * the count of undecided rows), so it cannot be captured into a CUDA graph. */
 enum { PKASP_NOALLOC_MAX_ROWS = 262144, PKASP_NOALLOC_MAX_NNZ = 4194304 };
 int pkasp_pmis_noalloc(int64_t n, const int64_t *ptr_dev, const int32_t *col_dev,
                        const uint8_t *strong_dev, uint64_t stream_id, int8_t *cf_dev,
@@ -339,7 +372,8 @@ int pkasp_pmis_noalloc(int64_t n, const int64_t *ptr_dev, const int32_t *col_dev
  * pkasp_assemble builds, for checks and tools.
  * ---------------------------------------------------------------------------------- */
 
-/* Sizes of the DOF map of a mesh (same arguments and conventions as pkasp_assemble):
+/* Sizes of the DOF map of a mesh (the nodes of V_h, Sec. 2; same arguments and
+ * conventions as pkasp_assemble):
  * sizes_out[6] = {n_all, n_h, n_H, nnz(A_h), nnz(A_H), nnz(Pi)}. If the output arrays
  * are non-NULL they are filled: dof_all_host[n_h], elem_dof_host[nt][nloc] (unknown index
  * or -1 per local node, nloc = (k+1)(k+2)(k+3)/6, local nodes = multi-indices m of |m| =
@@ -350,6 +384,14 @@ int pkasp_dofmap_host(const double *xyz_host, int64_t nv, const int32_t *tets_ho
                       int64_t *sizes_out, int64_t *dof_all_host, int32_t *elem_dof_host,
                       int64_t *ah_ptr_host, int32_t *ah_col_host, int64_t *pi_ptr_host,
                       int32_t *pi_col_host, double *pi_val_host);
+
+/* Coordinates of every P_k node of a mesh (same arguments and conventions as
+ * pkasp_assemble; Sec. 2): *n_all_out = number of nodes, boundary included; if
+ * node_xyz_host is non-NULL it receives [n_all][3] coordinates x = sum_a m_a v_a / k in
+ * the node numbering of pkasp_assemble, the order of f_nodal. Host only. Errors:
+ * EINVAL, EMESH. */
+int pkasp_nodes_host(const double *xyz_host, int64_t nv, const int32_t *tets_host, int64_t nt, int k,
+                     int64_t *n_all_out, double *node_xyz_host);
 
 /* The Taylor-Hood P_k - P_{k-1} blocks of Sec. 5 on the host, as pkasp_stokes_setup
  * assembles them (k = 2..4; mesh arguments as pkasp_assemble): sizes_out[4] = {n_h, n_p,
@@ -367,8 +409,9 @@ int pkasp_stokes_blocks_host(const double *xyz_host, int64_t nv, const int32_t *
  * Eq. (7) is kappa |T| sum_ab (grad lambda_a . grad lambda_b) S[a][b]. Host only. */
 int pkasp_reference_tensors(int k, double *S_out);
 
-/* Average device time (ms, CUDA events on `stream`) of `reps` back-to-back launches of
- * one hot-path kernel of the current setup: which = 0 fine SpMV, 1 fine smoother
+/* Measurement aid with no counterpart in the paper: average device time (ms, CUDA
+ * events on `stream`) of `reps` back-to-back launches of one hot-path kernel of the
+ * current setup: which = 0 fine SpMV, 1 fine smoother
  * (all colour phases of one S_k application), 2 V-cycle, 3 whole preconditioner; on the
  * multi-RHS blocks of the last solve with ncols > 1 (ESTATE before one): 4 blocked SpMM
  * Q = A_h P with its per-column dot (P, Q), 5 blocked fine smoother, 6 blocked

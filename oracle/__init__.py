@@ -95,6 +95,8 @@ def lib():
     L.orc_sgs.argtypes = [vp, i32p, C.c_int, f64p, f64p]
     L.orc_setup.restype = C.c_int
     L.orc_setup.argtypes = [vp, C.POINTER(OOpts)]
+    L.orc_set_max_iter.restype = C.c_int
+    L.orc_set_max_iter.argtypes = [vp, C.c_int]
     L.orc_levels.restype = C.c_int
     L.orc_levels.argtypes = [vp]
     L.orc_level_matrix.restype = vp
@@ -384,6 +386,12 @@ class Problem:
             raise RuntimeError(f"oracle setup failed ({rc})")
         self.opts = o
         return self
+
+    def set_max_iter(self, max_iter):
+        """Iteration cap of later solves, keeping the preconditioner: a solve stopped
+        after j iterations returns the iterate x_j."""
+        if lib().orc_set_max_iter(self.h, int(max_iter)) != 0:
+            raise RuntimeError("set_max_iter needs a setup and max_iter >= 1")
 
     def levels(self):
         return int(lib().orc_levels(self.h))

@@ -1572,6 +1572,15 @@ ocsr *orc_truncate(const ocsr *p, double tf, int pmax) {
     return t;
 }
 
+/* Changes the iteration cap of the solve without rebuilding the preconditioner (a solve
+ * from x0 stopped after j iterations leaves the iterate x_j of Algorithm 2.1's outer
+ * iteration, used to compare iterates one by one). */
+int orc_set_max_iter(oproblem *P, int max_iter) {
+    if (!P->have_setup || max_iter < 1) return 1;
+    P->o.max_iter = max_iter;
+    return 0;
+}
+
 int orc_setup(oproblem *P, const oopts *o) {
     free_levels(P);
     P->o = *o;

@@ -77,6 +77,7 @@ void orc_sgs(const ocsr *a, const int32_t *colour, int ncolour, const double *r,
 
 /* setup + solve */
 int orc_setup(oproblem *p, const oopts *o);
+int orc_set_max_iter(oproblem *p, int max_iter);
 int orc_levels(const oproblem *p);
 const ocsr *orc_level_matrix(const oproblem *p, int l, int which); /* 0 A_l, 1 P_l */
 void orc_level_info(const oproblem *p, int l, int64_t *out4);

@@ -8,7 +8,7 @@ and streams only.
 """
 from . import _lib
 from ._lib import PkaspError, default_options, load
-from .solver import Problem, dofmap_host, pmis, reference_tensors
+from .solver import Problem, dofmap_host, nodes_host, pmis, reference_tensors
 
-__all__ = ["Problem", "PkaspError", "default_options", "load", "pmis", "dofmap_host",
+__all__ = ["Problem", "PkaspError", "default_options", "load", "pmis", "dofmap_host", "nodes_host",
            "reference_tensors", "_lib"]

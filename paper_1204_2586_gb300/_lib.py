@@ -20,7 +20,7 @@ MODE_ADDITIVE, MODE_MULTIPLICATIVE = 0, 1
 SMOOTHER_SGS, SMOOTHER_L1JACOBI = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
 KRYLOV_CG, KRYLOV_FGMRES = 0, 1
-SOURCE_NONE, SOURCE_SINE = 0, 1
+SOURCE_NONE, SOURCE_SINE, SOURCE_NODAL = 0, 1, 2
 MAX_LEVELS, MAX_COLS = 25, 64
 
 
@@ -64,7 +64,7 @@ PF64 = C.POINTER(C.c_double)
 SIGNATURES = [
     ("pkasp_default_options", None, [C.POINTER(pkasp_options)]),
     ("pkasp_last_error", C.c_int, [C.c_char_p, C.c_size_t]),
-    ("pkasp_assemble", C.c_int, [vp, i64, vp, i64, C.c_int, vp, C.c_int, C.POINTER(vp)]),
+    ("pkasp_assemble", C.c_int, [vp, i64, vp, i64, C.c_int, vp, C.c_int, vp, C.POINTER(vp)]),
     ("pkasp_problem_info", C.c_int, [vp, C.POINTER(pkasp_info)]),
     ("pkasp_get_dofmap", C.c_int, [vp, vp, vp]),
     ("pkasp_get_rhs", C.c_int, [vp, vp, vp]),
@@ -73,7 +73,7 @@ SIGNATURES = [
     ("pkasp_solve", C.c_int, [vp, vp, vp, C.c_int, i64, C.POINTER(pkasp_stats), vp]),
     ("pkasp_solve_from_zero", C.c_int, [vp, vp, vp, C.c_int, i64, C.POINTER(pkasp_stats), vp]),
     ("pkasp_solve_adjoint", C.c_int, [vp, vp, vp, C.c_int, i64, C.POINTER(pkasp_stats), vp]),
-    ("pkasp_grad_kappa", C.c_int, [vp, vp, vp, vp, vp]),
+    ("pkasp_grad_kappa", C.c_int, [vp, vp, vp, C.c_int, i64, vp, vp]),
     ("pkasp_destroy", C.c_int, [vp]),
     ("pkasp_spmv", C.c_int, [vp, vp, vp, vp]),
     ("pkasp_apply_prec", C.c_int, [vp, vp, vp, vp]),
@@ -85,6 +85,7 @@ SIGNATURES = [
     ("pkasp_pmis", C.c_int, [i64, vp, vp, vp, C.c_uint64, vp, vp]),
     ("pkasp_pmis_noalloc", C.c_int, [i64, vp, vp, vp, C.c_uint64, vp, vp]),
     ("pkasp_dofmap_host", C.c_int, [vp, i64, vp, i64, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp]),
+    ("pkasp_nodes_host", C.c_int, [vp, i64, vp, i64, C.c_int, PI64, vp]),
     ("pkasp_reference_tensors", C.c_int, [C.c_int, vp]),
     ("pkasp_stokes_blocks_host", C.c_int, [vp, i64, vp, i64, C.c_int, vp, vp, vp, vp, vp, vp, vp]),
     ("pkasp_time_kernel", C.c_int, [vp, C.c_int, C.c_int, C.POINTER(C.c_float), vp]),

@@ -17,9 +17,10 @@ from .solver import Problem
 class PkPoissonSolve(torch.autograd.Function):
     """u = PkPoissonSolve.apply(kappa, b, problem, setup_kwargs)
 
-    kappa: [n_tets] float64 (CUDA or CPU), b: [n_h] float64 CUDA load vector, or
-    [n_h, ncols] for several right-hand sides solved as one block (then dL/dkappa is the
-    sum of the columns' gradients, dL/db the block of adjoint solutions).
+    kappa: [n_tets] float64 (CUDA or CPU; a CUDA tensor reaches the library as a device
+    pointer), b: [n_h] float64 CUDA load vector, or [n_h, ncols] for several right-hand
+    sides solved as one block (then dL/dkappa is the sum of the columns' gradients,
+    summed by the library, and dL/db the block of adjoint solutions).
     problem: an assembled :class:`Problem`; it is re-assembled for this kappa and its
     preconditioner rebuilt on every forward call.
     """
@@ -27,7 +28,7 @@ class PkPoissonSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, kappa, b, problem: Problem, setup_kwargs=None):
         kw = dict(setup_kwargs or {})
-        problem.set_kappa(kappa.detach().double().cpu().numpy())
+        problem.set_kappa(kappa.detach())
         problem.setup(**kw)
         u, st = problem.solve(b.detach().contiguous())
         ctx.problem = problem
@@ -42,12 +43,7 @@ class PkPoissonSolve(torch.autograd.Function):
         problem = ctx.problem
         (u,) = ctx.saved_tensors
         lam, _ = problem.solve_adjoint(g.contiguous())
-        if u.ndim == 1:
-            dkappa = problem.grad_kappa(u, lam)
-        else:
-            dkappa = problem.grad_kappa(u[:, 0].contiguous(), lam[:, 0].contiguous())
-            for c in range(1, u.shape[1]):
-                dkappa = dkappa + problem.grad_kappa(u[:, c].contiguous(), lam[:, c].contiguous())
+        dkappa = problem.grad_kappa(u, lam)
         return dkappa.to(device=ctx.kappa_device, dtype=ctx.kappa_dtype), lam, None, None
 
 

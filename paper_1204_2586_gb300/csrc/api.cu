@@ -87,14 +87,16 @@ int pkasp_last_error(char *buf, size_t n) {
 }
 
 int pkasp_assemble(const double *xyz_host, int64_t nv, const int32_t *tets_host, int64_t nt, int k,
-                   const double *kappa, int source, pkasp_problem **out) {
+                   const double *kappa, int source, const double *f_nodal, pkasp_problem **out) {
     if (!out) return set_error(PKASP_EINVAL, "out is NULL");
     *out = nullptr;
     if (!xyz_host || !tets_host || !kappa) return set_error(PKASP_EINVAL, "NULL mesh or kappa array");
     if (nv <= 0 || nt <= 0) return set_error(PKASP_EINVAL, "empty mesh");
     if (k < 1 || k > 4) return set_error(PKASP_EINVAL, "degree k must be 1..4");
-    if (source != PKASP_SOURCE_NONE && source != PKASP_SOURCE_SINE)
+    if (source != PKASP_SOURCE_NONE && source != PKASP_SOURCE_SINE && source != PKASP_SOURCE_NODAL)
         return set_error(PKASP_EINVAL, "unknown source");
+    if ((source == PKASP_SOURCE_NODAL) != (f_nodal != nullptr))
+        return set_error(PKASP_EINVAL, "f_nodal must be given exactly when source is PKASP_SOURCE_NODAL");
     for (int64_t i = 0; i < 4 * nt; ++i)
         if (tets_host[i] < 0 || tets_host[i] >= nv)
             return set_error(PKASP_EMESH, "tetrahedron vertex index out of range");
@@ -146,6 +148,13 @@ int pkasp_assemble(const double *xyz_host, int64_t nv, const int32_t *tets_host,
         up(p->d_vinc_ptr, D.vinc_ptr);
         p->d_vinc = pool.get<int32_t>(std::max<size_t>(D.vinc.size(), 1));
         up(p->d_vinc, D.vinc);
+        if (source == PKASP_SOURCE_NODAL) {
+            p->d_elem_all = pool.get<int32_t>(D.elem_all.size());
+            up(p->d_elem_all, D.elem_all);
+            p->d_fall = pool.get<double>(D.n_all);
+            PK_CUDA(cudaMemcpyAsync(p->d_fall, f_nodal, sizeof(double) * D.n_all,
+                                    is_device_ptr(f_nodal) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        }
         pk::dcsr_upload(pool, p->Ah, D.Ah_pattern, s);
         pk::dcsr_upload(pool, p->AH, D.AH_pattern, s);
         pk::dcsr_upload(pool, p->Pi, D.Pi, s);
@@ -295,16 +304,27 @@ static int solve_common(pkasp_problem *p, const double *b, double *x, int ncols,
             PK_CUDA(cudaMemcpyAsync(p->stage_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
             bb = p->stage_b;
         }
+        // from zero: only the ncols columns are zeroed (and, for a host x, copied back),
+        // so padding columns of an [n][ld] array and memory past a column-sliced view's
+        // last row are never written
+        auto zero_cols = [&](double *a) {
+            if (ld == ncols) PK_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * n, s));
+            else PK_CUDA(cudaMemset2DAsync(a, sizeof(double) * ld, 0, sizeof(double) * ncols, p->nh, s));
+        };
         if (!xd) {
             xx = p->stage_x;
-            if (from_zero) PK_CUDA(cudaMemsetAsync(xx, 0, sizeof(double) * n, s));
+            if (from_zero) zero_cols(xx);
             else PK_CUDA(cudaMemcpyAsync(xx, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
         } else if (from_zero) {
-            PK_CUDA(cudaMemsetAsync(xx, 0, sizeof(double) * n, s));
+            zero_cols(xx);
         }
         int rc = pk::solve_device(p, bb, xx, ncols, ld, st, s);
         if (!xd) {
-            PK_CUDA(cudaMemcpyAsync(x, xx, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+            if (from_zero && ld != ncols)
+                PK_CUDA(cudaMemcpy2DAsync(x, sizeof(double) * ld, xx, sizeof(double) * ld, sizeof(double) * ncols,
+                                          p->nh, cudaMemcpyDeviceToHost, s));
+            else
+                PK_CUDA(cudaMemcpyAsync(x, xx, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
             PK_CUDA(cudaStreamSynchronize(s));
         }
         if (rc != PKASP_OK) {
@@ -331,11 +351,13 @@ int pkasp_solve_adjoint(pkasp_problem *p, const double *g, double *lambda, int n
     return solve_common(p, g, lambda, ncols, ld, st, stream);
 }
 
-int pkasp_grad_kappa(const pkasp_problem *p, const double *u_dev, const double *lambda_dev, double *dkappa_dev,
-                     pkasp_stream_t stream) {
+int pkasp_grad_kappa(const pkasp_problem *p, const double *u_dev, const double *lambda_dev, int ncols, int64_t ld,
+                     double *dkappa_dev, pkasp_stream_t stream) {
     if (!p || !u_dev || !lambda_dev || !dkappa_dev) return set_error(PKASP_EINVAL, "NULL argument");
+    if (ncols < 1 || ncols > PKASP_MAX_COLS) return set_error(PKASP_EINVAL, "ncols must be 1..64");
+    if (ld < ncols) return set_error(PKASP_EINVAL, "ld must be >= ncols");
     return guarded([&]() -> int {
-        pk::grad_kappa_device(p, u_dev, lambda_dev, dkappa_dev, (cudaStream_t)stream);
+        pk::grad_kappa_device(p, u_dev, lambda_dev, ncols, ld, dkappa_dev, (cudaStream_t)stream);
         return PKASP_OK;
     });
 }
@@ -543,6 +565,35 @@ int pkasp_dofmap_host(const double *xyz_host, int64_t nv, const int32_t *tets_ho
         if (pi_ptr_host) memcpy(pi_ptr_host, D.Pi.ptr.data(), sizeof(int64_t) * (D.nh + 1));
         if (pi_col_host) memcpy(pi_col_host, D.Pi.col.data(), sizeof(int32_t) * D.Pi.col.size());
         if (pi_val_host) memcpy(pi_val_host, D.Pi.val.data(), sizeof(double) * D.Pi.val.size());
+        return PKASP_OK;
+    });
+}
+
+int pkasp_nodes_host(const double *xyz_host, int64_t nv, const int32_t *tets_host, int64_t nt, int k,
+                     int64_t *n_all_out, double *node_xyz_host) {
+    if (!xyz_host || !tets_host || !n_all_out) return set_error(PKASP_EINVAL, "NULL argument");
+    if (nv <= 0 || nt <= 0 || k < 1 || k > 4) return set_error(PKASP_EINVAL, "bad sizes or degree");
+    for (int64_t i = 0; i < 4 * nt; ++i)
+        if (tets_host[i] < 0 || tets_host[i] >= nv)
+            return set_error(PKASP_EMESH, "tetrahedron vertex index out of range");
+    return guarded([&]() -> int {
+        pk::DofMap D;
+        pk::HostMesh M{k, nv, nt, xyz_host, tets_host};
+        pk::build_dofmap(M, D);
+        *n_all_out = D.n_all;
+        if (!node_xyz_host) return PKASP_OK;
+        std::vector<int> m4;
+        pk::ref_nodes(k, m4);
+        const int nl = pk::nloc_of(k);
+        for (int64_t t = 0; t < nt; ++t)
+            for (int m = 0; m < nl; ++m) {
+                const int64_t d = D.elem_all[t * nl + m];
+                for (int c = 0; c < 3; ++c) {
+                    double v = 0;
+                    for (int a = 0; a < 4; ++a) v += m4[4 * m + a] * xyz_host[3 * (int64_t)tets_host[4 * t + a] + c];
+                    node_xyz_host[3 * d + c] = v / k;
+                }
+            }
         return PKASP_OK;
     });
 }

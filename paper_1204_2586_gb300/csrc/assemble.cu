@@ -184,6 +184,37 @@ __global__ void k_element_load(int64_t nt, int nl, int nq, const double *__restr
     }
 }
 
+// Element load vectors for a caller's f given at the P_k nodes (PKASP_SOURCE_NODAL):
+// f_h = sum_n f_n phi_n is evaluated at each quadrature point through the basis, then
+// be[t][m] = 6|T| sum_q w_q f_h(x_q) phi_m(lambda_q); one warp per element.
+__global__ void k_element_load_nodal(int64_t nt, int nl, int nq, const int32_t *__restrict__ elem_all,
+                                     const double *__restrict__ fall, const double *__restrict__ gf,
+                                     const double *__restrict__ wq, const double *__restrict__ phiq,
+                                     double *__restrict__ be) {
+    extern __shared__ double fsh[];  // [warps][nq]
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double *fq = fsh + (int64_t)wid * nq;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp; t < nt; t += nwarps) {
+        const int32_t *ea = elem_all + t * nl;
+        for (int q = lane; q < nq; q += 32) {
+            double v = 0.0;
+            for (int n = 0; n < nl; ++n) v = __dadd_rn(v, __dmul_rn(fall[ea[n]], phiq[(int64_t)q * nl + n]));
+            fq[q] = v;
+        }
+        __syncwarp();
+        const double vol = gf[t * kGF + 16];
+        for (int m = lane; m < nl; m += 32) {
+            double acc = 0.0;
+            for (int q = 0; q < nq; ++q)
+                acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(wq[q], fq[q]), phiq[(int64_t)q * nl + m]));
+            be[t * nl + m] = __dmul_rn(__dmul_rn(6.0, vol), acc);
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void k_gather_load(int64_t nrows, int nl, const int64_t *__restrict__ inc_ptr,
                               const int32_t *__restrict__ inc, const double *__restrict__ be,
                               double *__restrict__ b) {
@@ -197,31 +228,37 @@ __global__ void k_gather_load(int64_t nrows, int nl, const int64_t *__restrict__
     b[i] = s;
 }
 
-// dL/dkappa_e = -lambda_e^T Khat_e u_e, one warp per element (lanes over rows m).
+// dL/dkappa_e = -sum_c lambda_{c,e}^T Khat_e u_{c,e} over the ncols columns of u and
+// lambda ([n][ld], column c at offset c), one warp per element (lanes over rows m). Each
+// column's term is formed as for one column and the terms are added in column order.
 __global__ void k_grad_kappa(int64_t nt, int nl, const int32_t *__restrict__ elem_dof,
                              const double *__restrict__ gf, const double *__restrict__ S,
-                             const double *__restrict__ u, const double *__restrict__ lam,
-                             double *__restrict__ g) {
+                             const double *__restrict__ u, const double *__restrict__ lam, int ncols,
+                             int64_t ld, double *__restrict__ g) {
     const int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t = warp; t < nt; t += nwarps) {
         const double *gt = gf + t * kGF;
         const int32_t *ed = elem_dof + t * nl;
-        double part = 0.0;
-        for (int m = lane; m < nl; m += 32) {
-            int32_t i = ed[m];
-            if (i < 0) continue;
-            double km = 0.0;
-            for (int n = 0; n < nl; ++n) {
-                int32_t j = ed[n];
-                if (j < 0) continue;
-                km += elem_entry(gt, 1.0, S, nl, m, n) * u[j];
+        double tot = 0.0;
+        for (int c = 0; c < ncols; ++c) {
+            double part = 0.0;
+            for (int m = lane; m < nl; m += 32) {
+                int32_t i = ed[m];
+                if (i < 0) continue;
+                double km = 0.0;
+                for (int n = 0; n < nl; ++n) {
+                    int32_t j = ed[n];
+                    if (j < 0) continue;
+                    km += elem_entry(gt, 1.0, S, nl, m, n) * u[(int64_t)j * ld + c];
+                }
+                part += lam[(int64_t)i * ld + c] * km;
             }
-            part += lam[i] * km;
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            tot += part;
         }
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) g[t] = -part;
+        if (lane == 0) g[t] = -tot;
     }
 }
 
@@ -255,12 +292,16 @@ void assemble_values(pkasp_problem *p, cudaStream_t s) {
         p->nH, p->d_vinc_ptr, p->d_vinc, p->d_elem_vdof, p->d_gfac, p->d_kappa, p->AH.ptr,
         p->AH.col, p->AH.val);
     PK_LAUNCH();
-    if (p->source == PKASP_SOURCE_SINE) {
+    if (p->source == PKASP_SOURCE_SINE || p->source == PKASP_SOURCE_NODAL) {
         double *be = nullptr;
         PK_CUDA(cudaMallocAsync((void **)&be, sizeof(double) * p->nt * p->nloc, s));
         size_t shm = sizeof(double) * (size_t)p->nq * 8;
-        k_element_load<<<grid_for(p->nt * 32, 256, big), 256, shm, s>>>(
-            p->nt, p->nloc, p->nq, p->d_xyz, p->d_tets, p->d_gfac, p->d_lamq, p->d_wq, p->d_phiq, be);
+        if (p->source == PKASP_SOURCE_SINE)
+            k_element_load<<<grid_for(p->nt * 32, 256, big), 256, shm, s>>>(
+                p->nt, p->nloc, p->nq, p->d_xyz, p->d_tets, p->d_gfac, p->d_lamq, p->d_wq, p->d_phiq, be);
+        else
+            k_element_load_nodal<<<grid_for(p->nt * 32, 256, big), 256, shm, s>>>(
+                p->nt, p->nloc, p->nq, p->d_elem_all, p->d_fall, p->d_gfac, p->d_wq, p->d_phiq, be);
         PK_LAUNCH();
         k_gather_load<<<grid_for(p->nh, 256, INT32_MAX), 256, 0, s>>>(p->nh, p->nloc, p->d_inc_ptr,
                                                                        p->d_inc, be, p->d_b);
@@ -293,10 +334,10 @@ void assemble_device(pkasp_problem *p, cudaStream_t s) {
     assemble_values(p, s);
 }
 
-void grad_kappa_device(const pkasp_problem *p, const double *u, const double *lam, double *g,
-                       cudaStream_t s) {
+void grad_kappa_device(const pkasp_problem *p, const double *u, const double *lam, int ncols, int64_t ld,
+                       double *g, cudaStream_t s) {
     k_grad_kappa<<<grid_for(p->nt * 32, 256, 152 * 64), 256, 0, s>>>(
-        p->nt, p->nloc, p->d_elem_dof, p->d_gfac, p->d_S, u, lam, g);
+        p->nt, p->nloc, p->d_elem_dof, p->d_gfac, p->d_S, u, lam, ncols, ld, g);
     PK_LAUNCH();
 }
 

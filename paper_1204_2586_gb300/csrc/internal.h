@@ -153,6 +153,8 @@ struct pkasp_problem {
     double *d_gfac = nullptr;  // [nt][17]: kappa|T| G_ab (16) and |T|
     double *d_S = nullptr;     // reference tensors [16][nloc][nloc]
     double *d_phiq = nullptr, *d_lamq = nullptr, *d_wq = nullptr;  // load quadrature
+    double *d_fall = nullptr;        // PKASP_SOURCE_NODAL: f at every P_k node [n_all]
+    int32_t *d_elem_all = nullptr;   // PKASP_SOURCE_NODAL: all-node index [nt*nloc]
     int nq = 0;
     // incidence unknown -> (tet, local) in ascending tet order
     int64_t *d_inc_ptr = nullptr, *d_vinc_ptr = nullptr;
@@ -274,8 +276,8 @@ void apply_prec(pkasp_problem *p, const double *r, double *z, cudaStream_t s);
 void apply_smoother(pkasp_problem *p, const double *r, double *z, cudaStream_t s);
 void apply_vcycle(pkasp_problem *p, const double *b, double *x, cudaStream_t s);
 void spmv_fine(pkasp_problem *p, const double *x, double *y, cudaStream_t s);
-void grad_kappa_device(const pkasp_problem *p, const double *u, const double *lam, double *g,
-                       cudaStream_t s);
+void grad_kappa_device(const pkasp_problem *p, const double *u, const double *lam, int ncols, int64_t ld,
+                       double *g, cudaStream_t s);
 void pmis_device(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_t *strong,
                  uint64_t stream_id, int8_t *cf, cudaStream_t s);
 void pmis_noalloc(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_t *strong, uint64_t stream_id,

@@ -7,9 +7,9 @@
 // splitting with its scratch in one file-scope device array of fixed size, which every
 // GPU that loads this library holds until the process exits.
 #include <cstring>
-#include <mutex>
 
 #include "internal.h"
+#include "pmis.cuh"
 
 namespace {
 
@@ -27,79 +27,45 @@ constexpr size_t kScratchBytes = align256(kOffUnd + sizeof(unsigned long long));
 
 static __device__ __align__(256) unsigned char g_pmis_scratch[kScratchBytes];
 
-// device address of g_pmis_scratch, looked up once per device (the name itself is only
-// a host-side stand-in in host code)
-std::mutex g_mu;
-void *g_addr[64] = {nullptr};
-
+// Device address of g_pmis_scratch on the current device. In host code the array's
+// name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress on every call: the lookup is cheap next to the per-round
+// synchronisations, and it stays right if the device's context was reset and the module
+// loaded again at another address.
 void *scratch_address() {
-    int dev = 0;
-    PK_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) pk::fail(PKASP_EINVAL, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_pmis_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            pk::fail(PKASP_ECUDA, std::string("cudaGetSymbolAddress of the PMIS scratch failed: ") +
-                                      cudaGetErrorString(e));
-        }
-        g_addr[dev] = p;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_pmis_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        pk::fail(PKASP_ECUDA, std::string("cudaGetSymbolAddress of the PMIS scratch failed: ") +
+                                  cudaGetErrorString(e));
     }
-    return g_addr[dev];
+    return p;
 }
 
 unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256 > 0 ? (n + 255) / 256 : 1); }
 
-__device__ __forceinline__ uint64_t mix64(uint64_t stream, uint64_t i) {
-    uint64_t z = stream + (i + 1ull) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
+// Row pointers must start at 0 and never decrease: the mirror pass writes one scratch
+// slot per entry, so a malformed ptr must not reach it (sets *bad = 3).
+__global__ void k_na_check_ptr(int64_t n, const int64_t *__restrict__ ptr, int *__restrict__ bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    if ((i == 0 && ptr[0] != 0) || (i > 0 && ptr[i] < ptr[i - 1])) atomicExch(bad, 3);
 }
 
+// the per-row rules are those of pkasp_pmis (pmis.cuh), with 32-bit mirror and measure
+// arrays to keep the fixed scratch small
 __global__ void k_na_mirror(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
                             int32_t *__restrict__ mirror, int *__restrict__ bad) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
-        const int32_t j = col[e];
-        int64_t lo = ptr[j], hi = ptr[j + 1];
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            if (col[mid] < (int32_t)i) lo = mid + 1;
-            else hi = mid;
-        }
-        if (lo >= ptr[j + 1] || col[lo] != (int32_t)i) {
-            atomicExch(bad, 1);
-            mirror[e] = (int32_t)e;
-        } else {
-            mirror[e] = (int32_t)lo;
-        }
-    }
+    if (i < n) pk::pmis_mirror_row<int32_t>(i, n, ptr, col, mirror, bad);
 }
 
 __global__ void k_na_init(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ mirror,
                           const uint8_t *__restrict__ strong, int32_t *__restrict__ mu, int8_t *__restrict__ cf,
                           unsigned long long *__restrict__ und) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t m = 0, d = 0;
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
-        d += strong[e];
-        m += strong[mirror[e]];
-    }
-    mu[i] = m;
-    const int8_t c = (d == 0 && m == 0) ? (int8_t)-1 : (int8_t)0;
-    cf[i] = c;
-    if (c == 0) atomicAdd(und, 1ull);
-}
-
-__device__ __forceinline__ bool beats(int32_t mi, uint64_t hi, int64_t i, int32_t mj, uint64_t hj, int64_t j) {
-    if (mi != mj) return mi > mj;
-    if (hi != hj) return hi > hj;
-    return i > j;
+    if (i < n && pk::pmis_init_row<int32_t>(i, ptr, mirror, strong, mu, cf)) atomicAdd(und, 1ull);
 }
 
 __global__ void k_na_select(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
@@ -107,22 +73,7 @@ __global__ void k_na_select(int64_t n, const int64_t *__restrict__ ptr, const in
                             const int32_t *__restrict__ mu, uint64_t stream, const int8_t *__restrict__ cf,
                             uint8_t *__restrict__ newc) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint8_t sel = 0;
-    if (cf[i] == 0) {
-        sel = 1;
-        const uint64_t hi = mix64(stream, (uint64_t)i);
-        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
-            const int32_t j = col[e];
-            if (j == i || cf[j] != 0) continue;
-            if (!strong[e] && !strong[mirror[e]]) continue;
-            if (!beats(mu[i], hi, i, mu[j], mix64(stream, (uint64_t)j), j)) {
-                sel = 0;
-                break;
-            }
-        }
-    }
-    newc[i] = sel;
+    if (i < n) newc[i] = pk::pmis_select_row<int32_t>(i, ptr, col, mirror, strong, mu, stream, cf);
 }
 
 __global__ void k_na_commit(int64_t n, const uint8_t *__restrict__ newc, int8_t *__restrict__ cf) {
@@ -134,13 +85,7 @@ __global__ void k_na_mark(int64_t n, const int64_t *__restrict__ ptr, const int3
                           const uint8_t *__restrict__ strong, const uint8_t *__restrict__ newc,
                           int8_t *__restrict__ cf, unsigned long long *__restrict__ und) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || cf[i] != 0) return;
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e)
-        if (strong[e] && newc[col[e]]) {
-            cf[i] = -1;
-            return;
-        }
-    atomicAdd(und, 1ull);
+    if (i < n && pk::pmis_mark_row(i, ptr, col, strong, newc, cf)) atomicAdd(und, 1ull);
 }
 
 }  // namespace
@@ -159,6 +104,7 @@ void pmis_noalloc(int64_t n, const int64_t *ptr, const int32_t *col, const uint8
     if (nnz > kMaxNnz)
         fail(PKASP_EINVAL, "pkasp_pmis_noalloc: " + std::to_string(nnz) +
                                " entries exceed the fixed scratch limit of " + std::to_string(kMaxNnz));
+    if (nnz < 0) fail(PKASP_EINVAL, "pkasp_pmis_noalloc: ptr[n] is negative");
     if (n == 0) return;
     int32_t *mirror = reinterpret_cast<int32_t *>(base + kOffMirror);
     int32_t *mu = reinterpret_cast<int32_t *>(base + kOffMu);
@@ -168,6 +114,14 @@ void pmis_noalloc(int64_t n, const int64_t *ptr, const int32_t *col, const uint8
     // the array keeps the previous call's contents: clear the two counters
     PK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     PK_CUDA(cudaMemsetAsync(und, 0, sizeof(unsigned long long), s));
+    {
+        k_na_check_ptr<<<blocks_for(n + 1), 256, 0, s>>>(n, ptr, bad);
+        PK_LAUNCH();
+        int hp = 0;
+        PK_CUDA(cudaMemcpyAsync(&hp, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PK_CUDA(cudaStreamSynchronize(s));
+        if (hp) fail(PKASP_EINVAL, "pkasp_pmis_noalloc: ptr must start at 0 and never decrease");
+    }
     k_na_mirror<<<blocks_for(n), 256, 0, s>>>(n, ptr, col, mirror, bad);
     PK_LAUNCH();
     k_na_init<<<blocks_for(n), 256, 0, s>>>(n, ptr, mirror, strong, mu, cf, und);
@@ -177,7 +131,9 @@ void pmis_noalloc(int64_t n, const int64_t *ptr, const int32_t *col, const uint8
     PK_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaMemcpyAsync(&left, und, sizeof(left), cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaStreamSynchronize(s));
-    if (hb) fail(PKASP_EINVAL, "pkasp_pmis_noalloc needs a structurally symmetric matrix");
+    if (hb == 2) fail(PKASP_EINVAL, "pkasp_pmis_noalloc: a column index lies outside [0, n)");
+    if (hb) fail(PKASP_EINVAL, "pkasp_pmis_noalloc needs a structurally symmetric pattern with ascending columns "
+                               "in every row");
     int64_t rounds = 0;
     while (left > 0) {
         PK_CUDA(cudaMemsetAsync(und, 0, sizeof(unsigned long long), s));

@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "pmis.cuh"
 
 namespace pk {
 
@@ -26,21 +27,6 @@ unsigned blocks_for(int64_t n, int per) {
     return (unsigned)std::max<int64_t>(1, b);
 }
 
-__device__ __forceinline__ uint64_t splitmix64(uint64_t stream, uint64_t i) {
-    uint64_t z = stream + (i + 1ull) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ int64_t lower_bound_col(const int32_t *col, int64_t lo, int64_t hi, int32_t j) {
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (col[mid] < j) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
 
 // ---------------------------------------------------------------------------------
 // Jones-Plassmann colouring: priority (hash, -index); each round the local maxima among
@@ -188,48 +174,21 @@ __global__ void k_strength(int64_t n, const int64_t *__restrict__ ptr, const int
     }
 }
 
-// mirror[e] = position of (j, i) for e = (i, j); the pattern must be symmetric
+// ---------------------------------------------------------------------------------
+// PMIS (De Sterck, Yang & Heys 2006), one thread per row; the per-row rules are in
+// pmis.cuh (shared with the fixed-scratch entry point).
+// ---------------------------------------------------------------------------------
 __global__ void k_mirror(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
                          int64_t *__restrict__ mirror, int *__restrict__ bad) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
-        int32_t j = col[e];
-        int64_t q = lower_bound_col(col, ptr[j], ptr[j + 1], (int32_t)i);
-        if (q >= ptr[j + 1] || col[q] != i) {
-            atomicExch(bad, 1);
-            mirror[e] = e;
-        } else {
-            mirror[e] = q;
-        }
-    }
+    if (i < n) pmis_mirror_row<int64_t>(i, n, ptr, col, mirror, bad);
 }
 
-// ---------------------------------------------------------------------------------
-// PMIS (De Sterck, Yang & Heys 2006). Measure (|S_i^T|, hash, i) compared
-// lexicographically; isolated points (no strong connection either way) are F.
-// ---------------------------------------------------------------------------------
 __global__ void k_pmis_init(int64_t n, const int64_t *__restrict__ ptr, const int64_t *__restrict__ mirror,
                             const uint8_t *__restrict__ strong, int64_t *__restrict__ mu,
                             int8_t *__restrict__ cf, unsigned long long *__restrict__ undecided) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t m = 0, d = 0;
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
-        d += strong[e];
-        m += strong[mirror[e]];
-    }
-    mu[i] = m;
-    int8_t c = (d == 0 && m == 0) ? (int8_t)-1 : (int8_t)0;
-    cf[i] = c;
-    if (c == 0) atomicAdd(undecided, 1ull);
-}
-
-__device__ __forceinline__ bool meas_beats(int64_t mi, uint64_t hi, int64_t i, int64_t mj, uint64_t hj,
-                                           int64_t j) {
-    if (mi != mj) return mi > mj;
-    if (hi != hj) return hi > hj;
-    return i > j;
+    if (i < n && pmis_init_row<int64_t>(i, ptr, mirror, strong, mu, cf)) atomicAdd(undecided, 1ull);
 }
 
 __global__ void k_pmis_select(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
@@ -237,23 +196,7 @@ __global__ void k_pmis_select(int64_t n, const int64_t *__restrict__ ptr, const 
                               const int64_t *__restrict__ mu, uint64_t stream, const int8_t *__restrict__ cf,
                               uint8_t *__restrict__ newc) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint8_t sel = 0;
-    if (cf[i] == 0) {
-        sel = 1;
-        const uint64_t hi = splitmix64(stream, (uint64_t)i);
-        const int64_t mi = mu[i];
-        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
-            int32_t j = col[e];
-            if (j == i || cf[j] != 0) continue;
-            if (!strong[e] && !strong[mirror[e]]) continue;
-            if (!meas_beats(mi, hi, i, mu[j], splitmix64(stream, (uint64_t)j), j)) {
-                sel = 0;
-                break;
-            }
-        }
-    }
-    newc[i] = sel;
+    if (i < n) newc[i] = pmis_select_row<int64_t>(i, ptr, col, mirror, strong, mu, stream, cf);
 }
 
 __global__ void k_pmis_commit(int64_t n, const uint8_t *__restrict__ newc, int8_t *__restrict__ cf) {
@@ -265,13 +208,7 @@ __global__ void k_pmis_mark_f(int64_t n, const int64_t *__restrict__ ptr, const 
                               const uint8_t *__restrict__ strong, const uint8_t *__restrict__ newc,
                               int8_t *__restrict__ cf, unsigned long long *__restrict__ undecided) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || cf[i] != 0) return;
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e)
-        if (strong[e] && newc[col[e]]) {
-            cf[i] = -1;
-            return;
-        }
-    atomicAdd(undecided, 1ull);
+    if (i < n && pmis_mark_row(i, ptr, col, strong, newc, cf)) atomicAdd(undecided, 1ull);
 }
 
 __global__ void k_flag_c(int64_t n, const int8_t *__restrict__ cf, int64_t *__restrict__ out) {
@@ -837,7 +774,8 @@ void pmis_run(int64_t n, const int64_t *ptr, const int32_t *col, const uint8_t *
         PK_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
         PK_CUDA(cudaMemcpyAsync(&left, und, sizeof(left), cudaMemcpyDeviceToHost, s));
         PK_CUDA(cudaStreamSynchronize(s));
-        if (hb) fail(PKASP_EINVAL, "PMIS needs a structurally symmetric matrix");
+        if (hb == 2) fail(PKASP_EINVAL, "PMIS: a column index lies outside [0, n)");
+        if (hb) fail(PKASP_EINVAL, "PMIS needs a structurally symmetric pattern with ascending columns in every row");
         int rounds = 0;
         while (left > 0) {
             PK_CUDA(cudaMemsetAsync(und, 0, sizeof(unsigned long long), s));

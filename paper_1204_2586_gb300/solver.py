@@ -16,15 +16,29 @@ def _ptr(t) -> int:
 def _row_stride(a) -> int:
     """Elements between consecutive rows of a [n] or [n, ncols] array (the ABI's ld);
     columns must be adjacent."""
-    if a.ndim == 1:
-        return 1
     if hasattr(a, "stride") and callable(a.stride):
         st = a.stride()
     else:
         st = tuple(s // a.itemsize for s in a.strides)
+    if a.ndim == 1:
+        return st[0]  # one column of a wider block is a strided vector
     if a.shape[1] > 1 and st[1] != 1:
         raise ValueError("columns of a multi-RHS block must be adjacent (stride 1)")
     return st[0]
+
+
+def _f64_arg(a):
+    """(keep-alive object, pointer) of a float64 array for a host-or-device argument: a
+    CUDA tensor is passed as its device pointer, anything else as contiguous host data."""
+    import torch
+
+    if isinstance(a, torch.Tensor):
+        t = a.detach().to(torch.float64).contiguous()
+        if t.is_cuda:
+            return t, t.data_ptr()
+        a = t.numpy()
+    h = np.ascontiguousarray(a, dtype=np.float64)
+    return h, h.ctypes.data
 
 
 def _stream(stream=None):
@@ -37,18 +51,24 @@ def _stream(stream=None):
 class Problem:
     """An assembled P_k problem (Eq. 7 of Lee, Leng & Zhang) living on the GPU."""
 
-    def __init__(self, xyz, tets, k, kappa=None, source=L.SOURCE_SINE):
+    def __init__(self, xyz, tets, k, kappa=None, source=L.SOURCE_SINE, f_nodal=None):
+        """kappa: [nt] (host array or CUDA tensor, default 1); f_nodal: the source f at
+        every P_k node ([n_all], the order of :func:`nodes_host`; host array or CUDA
+        tensor), which selects PKASP_SOURCE_NODAL."""
         import torch
 
         lib = L.load()
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         tets = np.ascontiguousarray(tets, dtype=np.int32)
         nt = tets.shape[0]
-        kap = np.ascontiguousarray(np.ones(nt) if kappa is None else kappa, dtype=np.float64)
+        kap, kp = _f64_arg(np.ones(nt) if kappa is None else kappa)
+        fn, fp = (None, None) if f_nodal is None else _f64_arg(f_nodal)
+        if f_nodal is not None:
+            source = L.SOURCE_NODAL
         torch.cuda.init()
         h = C.c_void_p()
         L.check(lib.pkasp_assemble(xyz.ctypes.data, xyz.shape[0], tets.ctypes.data, nt, k,
-                                   kap.ctypes.data, source, C.byref(h)))
+                                   kp, source, fp, C.byref(h)))
         self.h = h
         self.k = k
         self.nt = nt
@@ -120,8 +140,9 @@ class Problem:
         return cf, st[:nnz]
 
     def set_kappa(self, kappa, stream=None):
-        kap = np.ascontiguousarray(kappa, dtype=np.float64)
-        L.check(L.load().pkasp_set_kappa(self.h, kap.ctypes.data, _stream(stream)))
+        """kappa: [nt] host array or CUDA tensor (a device tensor is passed as it is)."""
+        kap, kp = _f64_arg(kappa)
+        L.check(L.load().pkasp_set_kappa(self.h, kp, _stream(stream)))
         self.opts = None
 
     # ---- setup / solve ----------------------------------------------------------
@@ -252,10 +273,16 @@ class Problem:
         return x
 
     def grad_kappa(self, u, lam, stream=None):
+        """dL/dkappa_e = -sum_c lambda_{c,e}^T Khat_e u_{c,e} for u, lam CUDA tensors [n_h]
+        or [n_h, ncols] (one row stride); the column sum runs in the library."""
         import torch
 
+        ncols = 1 if u.ndim == 1 else u.shape[1]
+        ld = _row_stride(u)
+        if _row_stride(lam) != ld or lam.shape != u.shape:
+            raise ValueError("u and lam must have one shape and row stride")
         g = torch.empty(self.nt, dtype=torch.float64, device=u.device)
-        L.check(L.load().pkasp_grad_kappa(self.h, _ptr(u), _ptr(lam), _ptr(g), _stream(stream)))
+        L.check(L.load().pkasp_grad_kappa(self.h, _ptr(u), _ptr(lam), ncols, ld, _ptr(g), _stream(stream)))
         return g
 
     def time_kernel(self, which, reps=20, stream=None):
@@ -297,6 +324,21 @@ def dofmap_host(xyz, tets, k):
                                   pp.ctypes.data, pc.ctypes.data, pv.ctypes.data))
     return dict(n_all=n_all, nh=nh, nH=nH, nnz_H=nnz_H, dof_all=dof_all, elem_dof=elem,
                 ah_ptr=ap, ah_col=ac[:nnz_h], pi_ptr=pp, pi_col=pc[:nnz_pi], pi_val=pv[:nnz_pi])
+
+
+def nodes_host(xyz, tets, k):
+    """Coordinates [n_all, 3] of every P_k node of a mesh, in the node numbering of the
+    library (the order of a nodal source f_nodal)."""
+    lib = L.load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    n = C.c_int64()
+    L.check(lib.pkasp_nodes_host(xyz.ctypes.data, xyz.shape[0], tets.ctypes.data, tets.shape[0], k,
+                                 C.byref(n), None))
+    X = np.zeros((n.value, 3))
+    L.check(lib.pkasp_nodes_host(xyz.ctypes.data, xyz.shape[0], tets.ctypes.data, tets.shape[0], k,
+                                 C.byref(n), X.ctypes.data))
+    return X
 
 
 def stokes_blocks_host(xyz, tets, k):

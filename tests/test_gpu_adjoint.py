@@ -36,6 +36,59 @@ def test_grad_kappa_matches_oracle(torch_cuda, oracle_mod):
     G.close()
 
 
+def test_grad_kappa_columns_summed_on_device(torch_cuda, oracle_mod):
+    """pkasp_grad_kappa over a block of 3 columns in a [n_h][4] array (ld > ncols):
+    the library's column sum against the sum of the oracle's single-column gradients."""
+    torch = torch_cuda
+    from paper_1204_2586_gb300 import Problem
+
+    xyz, t = kuhn_mesh(3, 0.2, 0)
+    kap = kappa_lognormal(t.shape[0], 1)
+    G = Problem(xyz, t, 4, kap)
+    O = oracle_mod.Problem(xyz, t, 4, kap)
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal((G.nh, 4))
+    Lm = rng.standard_normal((G.nh, 4))
+    Ud, Ld = torch.tensor(U, device="cuda"), torch.tensor(Lm, device="cuda")
+    g = G.grad_kappa(Ud[:, :3], Ld[:, :3]).cpu().numpy()
+    go = sum(O.grad_kappa(U[:, c].copy(), Lm[:, c].copy()) for c in range(3))
+    assert np.abs(g - go).max() <= 1e-12 * np.abs(go).max()
+    # one column of the same block equals the single-column call bitwise
+    g1 = G.grad_kappa(Ud[:, 1], Ld[:, 1]).cpu().numpy()
+    g1c = G.grad_kappa(Ud[:, 1].contiguous(), Ld[:, 1].contiguous()).cpu().numpy()
+    assert np.array_equal(g1, g1c)
+    G.close()
+
+
+@pytest.mark.parametrize("k,n,ks", [(2, 5, None), (3, 3, 1), (4, 3, 1)])
+def test_nodal_source_load_matches_oracle(torch_cuda, oracle_mod, k, n, ks):
+    """A caller's f at the P_k nodes (PKASP_SOURCE_NODAL; here a smooth non-sine f with
+    a seeded random part) against the oracle's load b = <f_h, phi_i>, element by element
+    at 1e-12; a device f and a host f give the same load; set_kappa keeps the source."""
+    torch = torch_cuda
+    from paper_1204_2586_gb300 import Problem, nodes_host
+
+    xyz, t = kuhn_mesh(n, 0.2, 0)
+    kap = None if ks is None else kappa_lognormal(t.shape[0], ks)
+    X = nodes_host(xyz, t, k)
+    f = np.exp(X[:, 0]) * np.cos(2 * X[:, 1]) + X[:, 2] ** 3 + 0.1 * rhs_normal(X.shape[0], 1, 7)[:, 0]
+    G = Problem(xyz, t, k, kap, f_nodal=f)
+    Gd = Problem(xyz, t, k, kap, f_nodal=torch.tensor(f, device="cuda"))
+    O = oracle_mod.Problem(xyz, t, k, kap, source=oracle_mod.SOURCE_NONE)
+    O.set_source_nodal(f)
+    bo = O.rhs()
+    b = G.rhs().cpu().numpy()
+    assert np.abs(b - bo).max() <= 1e-12 * np.abs(bo).max()
+    assert np.array_equal(Gd.rhs().cpu().numpy(), b)
+    k2 = kappa_lognormal(t.shape[0], 9)
+    G.set_kappa(torch.tensor(k2, device="cuda"))
+    O.set_kappa(k2)
+    assert np.abs(G.rhs().cpu().numpy() - O.rhs()).max() <= 1e-12 * np.abs(bo).max()
+    assert np.abs(G.matrix(0)[2] - O.matrix(0).val).max() <= 1e-12 * np.abs(O.matrix(0).val).max()
+    G.close()
+    Gd.close()
+
+
 def _fd_check(torch, n, k, nfd, tol_rel, eps=1e-6):
     from paper_1204_2586_gb300 import Problem
     from paper_1204_2586_gb300.autograd import solve

@@ -161,3 +161,35 @@ def test_solve_from_zero_never_reads_x(gpu, ncols, where):
     assert np.array_equal(ref, out)
     assert st0["iters"] == st1["iters"] and all(s == 0 for s in st1["status"])
     G.close()
+
+
+@pytest.mark.parametrize("ncols", [1, 3])
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_solve_from_zero_leaves_padding_columns(gpu, ncols, where):
+    """x of [n_h][ld] with ld > ncols: pkasp_solve_from_zero writes only the ncols
+    solved columns; the padding columns keep their sentinel values, for host and device
+    x, and the solved columns equal pkasp_solve from a zero x of the same layout
+    bitwise."""
+    torch = gpu
+    from paper_1204_2586_gb300 import Problem
+    from paper_1204_2586_gb300.inputs import rhs_normal
+
+    G = Problem(*kuhn_mesh(4, 0.2, 0), 2)
+    G.setup()
+    ld = ncols + 2
+    Bw = np.full((G.nh, ld), 3.25)
+    Bw[:, :ncols] = rhs_normal(G.nh, ncols, 11)
+    Xw = np.full((G.nh, ld), -7.5)
+    X0 = np.zeros((G.nh, ld))
+    if where == "device":
+        bw, xw, x0 = (torch.tensor(a, device="cuda") for a in (Bw, Xw, X0))
+    else:
+        bw, xw, x0 = Bw, Xw, X0
+    _, st0 = G.solve(bw[:, :ncols], x0[:, :ncols])
+    _, st1 = G.solve(bw[:, :ncols], xw[:, :ncols], from_zero=True)
+    out = xw.cpu().numpy() if where == "device" else xw
+    ref = x0.cpu().numpy() if where == "device" else x0
+    assert np.all(out[:, ncols:] == -7.5)
+    assert np.array_equal(out[:, :ncols], ref[:, :ncols])
+    assert st0["iters"] == st1["iters"] and all(s == 0 for s in st1["status"])
+    G.close()

@@ -3,7 +3,8 @@ P4 measurement run them:
 
 * P4 on 48^3 jittered Kuhn cubes with kappa = exp(N(0,1)) (6,967,871 unknowns, 513M
   nonzeros): the operator pattern and sampled rows against the oracle's assembly, the
-  fine colouring bit-exact against the oracle's colouring of the same matrix, and the
+  fine colouring and the whole P1 AMG hierarchy (strength, C/F, level colours and
+  matrices) bit-exact against the oracle's setup of the same problem, and the
   FP64 and FP32-preconditioner solutions checked on the host against the oracle's own
   matrix and right-hand side (true residual <= 1e-8, the quantity every solve targets).
 * P2 on 64^3 cubes with 48 right-hand sides (2,048,383 unknowns per column): one column
@@ -56,10 +57,27 @@ def test_p4_operator_and_colouring(p4, oracle_mod):
     del gptr, gcol, gval
     bo = O.rhs()
     assert np.abs(G.rhs().cpu().numpy() - bo).max() <= 1e-12 * np.abs(bo).max()
+    # the whole preconditioner setup on both sides: fine colouring of A_h and the P1 AMG
+    # hierarchy on A_H (103,823 rows): level colourings, strength flags and C/F
+    # splittings bit-exact, level matrices and interpolation patterns exact, values 1e-12
     G.setup(level_smoother=1)
-    colour_o, ncol_o = oracle_mod.colour_jp(A, oracle_mod.stream_colour(0, 0))
+    O.setup(level_smoother=1)
     colour_g, ncol_g = G.colours(-1)
-    assert ncol_g == ncol_o and np.array_equal(colour_g, colour_o)
+    assert np.array_equal(colour_g, O.fine_colour()) and ncol_g == colour_g.max() + 1
+    assert G.info.levels == O.levels()
+    for l in range(O.levels()):
+        Lo = O.level(l)
+        c, nc = G.colours(l)
+        assert np.array_equal(c, Lo["colour"]) and nc == Lo["ncolour"], l
+        gp, gc, gv, _ = G.matrix(3 + 2 * l)
+        assert np.array_equal(gp, Lo["A"].ptr) and np.array_equal(gc, Lo["A"].col), l
+        assert np.abs(gv - Lo["A"].val).max() <= 1e-12 * np.abs(Lo["A"].val).max(), l
+        if "P" in Lo:
+            cf, st = G.splitting(l)
+            assert np.array_equal(st, Lo["strong"]) and np.array_equal(cf, Lo["cf"]), l
+            pp, pc, pv, _ = G.matrix(4 + 2 * l)
+            assert np.array_equal(pp, Lo["P"].ptr) and np.array_equal(pc, Lo["P"].col), l
+            assert np.abs(pv - Lo["P"].val).max() <= 1e-12 * np.abs(Lo["P"].val).max(), l
 
 
 @pytest.mark.slow

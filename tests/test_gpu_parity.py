@@ -10,7 +10,9 @@ from paper_1204_2586_gb300.inputs import kappa_lognormal, kuhn_mesh
 pytestmark = pytest.mark.gpu
 
 RTOL_OP = 1e-12     # assembled operators and single operator applications
-RTOL_ITER = 1e-10   # per-iteration residual norms of the FP64 solve
+RTOL_ITER = 1e-10   # per-iteration residual norms of the FP64 solve, relative to ||r_0||
+RTOL_X = 1e-10      # iterates x_j element by element, relative to max|x_j|, while
+                    # ||r_j|| >= 1e-3 ||r_0|| (later CG amplifies rounding differences)
 
 
 @pytest.fixture(scope="module")
@@ -273,3 +275,93 @@ def test_grid_stride_smoother_solve_history(pair, torch_cuda, mode, layout):
     m = min(len(h), len(ref["hist"]))
     assert (np.abs(h[:m] - ref["hist"][:m]) / ref["hist"][0]).max() <= RTOL_ITER
     assert np.linalg.norm(x.cpu().numpy() - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+
+
+def _iterates_match(G, O, b, js, **kw):
+    """x_j of the GPU solve against the oracle's x_j, element by element, for every j in
+    js: both solves start from x0 = 0 and stop after j iterations (max_iter = j), which
+    leaves the iterate x_j. Returns the largest relative deviation."""
+    worst = 0.0
+    for j in js:
+        G.setup(max_iter=j, **kw)
+        O.set_max_iter(j)
+        xo = O.solve()["x"]
+        x, st = G.solve(b, raise_on_fail=False)
+        assert st["iters"][0] == j
+        dev = np.abs(x.cpu().numpy() - xo).max() / np.abs(xo).max()
+        assert dev <= RTOL_X, (j, dev)
+        worst = max(worst, dev)
+    return worst
+
+
+def _early_iterations(hist, cap=40):
+    """Iteration counts j = 1, 2, 4, ... with ||r_j|| >= 1e-3 ||r_0|| in the oracle's
+    history (the range where element-wise agreement to 1e-10 is attainable)."""
+    js, j = [], 1
+    while j < len(hist) and j <= cap and hist[j] >= 1e-3 * hist[0]:
+        js.append(j)
+        j *= 2
+    return js
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_iterates_elementwise(pair, torch_cuda, mode):
+    """Per-iteration parity on the iterates themselves: max|x_j^GPU - x_j^oracle| <=
+    1e-10 max|x_j^oracle| for j = 1, 2, 4, ... while the residual is above 1e-3 ||r_0||
+    (additive and multiplicative forms)."""
+    _, G, O = pair
+    _setup_both(G, O, mode=mode)
+    ref = O.solve()
+    js = _early_iterations(ref["hist"])
+    assert js, "no early iteration to compare"
+    _iterates_match(G, O, G.rhs(), js, mode=mode)
+
+
+@pytest.fixture(scope="module")
+def p4_n24(torch_cuda, oracle_mod):
+    """P4 on 24^3 jittered Kuhn cubes with kappa = exp(N(0,1)) (seed 1): 857,375
+    unknowns, 63M nonzeros; its colour phases run several waves of row groups."""
+    from paper_1204_2586_gb300 import Problem
+
+    xyz, t = kuhn_mesh(24, 0.2, 0)
+    kap = kappa_lognormal(t.shape[0], 1)
+    G = Problem(xyz, t, 4, kap)
+    O = oracle_mod.Problem(xyz, t, 4, kap)
+    yield G, O
+    G.close()
+
+
+@pytest.mark.slow
+def test_p4_n24_hierarchy_history_and_iterates(p4_n24):
+    """P4 at a size where every colour phase runs several waves: fine colouring, level
+    colourings, strength flags, C/F splittings and interpolation patterns bit-exact;
+    residual history within 1e-10 ||r_0||, iterations +-1; iterates element by element
+    at 1e-10 while ||r_j|| >= 1e-3 ||r_0||."""
+    G, O = p4_n24
+    _setup_both(G, O, level_smoother=1)
+    gc, _ = G.colours(-1)
+    assert np.array_equal(gc, O.fine_colour())
+    assert G.info.levels == O.levels()
+    for l in range(O.levels()):
+        Lo = O.level(l)
+        c, nc = G.colours(l)
+        assert np.array_equal(c, Lo["colour"]) and nc == Lo["ncolour"], l
+        val = _csr_equal_pattern(G.matrix(3 + 2 * l), Lo["A"])
+        _rel_close(val, Lo["A"].val, RTOL_OP)
+        if "P" in Lo:
+            cf, st = G.splitting(l)
+            assert np.array_equal(st, Lo["strong"]) and np.array_equal(cf, Lo["cf"]), l
+            _csr_equal_pattern(G.matrix(4 + 2 * l), Lo["P"])
+    ref = O.solve()
+    assert ref["status"] == 0
+    b = G.rhs()
+    x, st = G.solve(b, hist_cap=600)
+    assert st["status"][0] == 0 and abs(st["iters"][0] - ref["iters"]) <= 1
+    h = st["hist"][:, 0]
+    m = min(len(h), len(ref["hist"]))
+    dev = np.abs(h[:m] - ref["hist"][:m]) / ref["hist"][0]
+    assert dev.max() <= RTOL_ITER, dev.max()
+    assert np.linalg.norm(x.cpu().numpy() - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    js = _early_iterations(ref["hist"], cap=16)
+    worst = _iterates_match(G, O, b, js, level_smoother=1)
+    print(f"P4 24^3: {ref['iters']} iterations, history dev {dev.max():.2e}, iterates {js} dev {worst:.2e}")

@@ -79,6 +79,22 @@ def test_dofmap_matches_oracle(lib, oracle_mod, k, n):
     assert np.array_equal(D["pi_val"], Pi.val)
 
 
+@pytest.mark.parametrize("k,n", [(1, 3), (2, 3), (3, 2), (4, 2)])
+def test_nodes_match_oracle(lib, oracle_mod, k, n):
+    """Coordinates of every P_k node in the library's node numbering (the order of a
+    nodal source) against the oracle's, bit-exact (both form sum_a m_a v_a / k in the
+    same order), and against the unknowns' coordinates of the DOF map."""
+    from paper_1204_2586_gb300.solver import nodes_host
+
+    xyz, t = kuhn_mesh(n, 0.2, 0)
+    X = nodes_host(xyz, t, k)
+    P = oracle_mod.Problem(xyz, t, k, source=0)
+    assert X.shape == (P.nall, 3)
+    assert np.array_equal(X, P.nodes())
+    dof_all, dx = P.dofs()
+    assert np.array_equal(X[dof_all], dx)
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
 def test_reference_tensors_match_oracle(lib, oracle_mod, k):
     """The library integrates by Grundmann-Moeller quadrature, the oracle by exact
@@ -125,11 +141,24 @@ def test_host_argument_errors(lib):
     h = C.c_void_p()
     kap = np.ones(t.shape[0])
     rc = lib.pkasp_assemble(xyz.ctypes.data, xyz.shape[0], bad.ctypes.data, t.shape[0], 2, kap.ctypes.data, 1,
-                            C.byref(h))
+                            None, C.byref(h))
     assert rc == L.PKASP_EMESH and not h.value
     rc = lib.pkasp_assemble(xyz.ctypes.data, xyz.shape[0], t.ctypes.data, t.shape[0], 0, kap.ctypes.data, 1,
-                            C.byref(h))
+                            None, C.byref(h))
     assert rc == L.PKASP_EINVAL
+    # a nodal source needs its values, and values need the nodal source
+    f = np.ones(1000)
+    rc = lib.pkasp_assemble(xyz.ctypes.data, xyz.shape[0], t.ctypes.data, t.shape[0], 2, kap.ctypes.data,
+                            L.SOURCE_NODAL, None, C.byref(h))
+    assert rc == L.PKASP_EINVAL and "f_nodal" in L.last_error()
+    rc = lib.pkasp_assemble(xyz.ctypes.data, xyz.shape[0], t.ctypes.data, t.shape[0], 2, kap.ctypes.data,
+                            L.SOURCE_SINE, f.ctypes.data, C.byref(h))
+    assert rc == L.PKASP_EINVAL and not h.value
+    rc = lib.pkasp_grad_kappa(None, None, None, 1, 1, None, None)
+    assert rc == L.PKASP_EINVAL
+    n = C.c_int64()
+    rc = lib.pkasp_nodes_host(xyz.ctypes.data, xyz.shape[0], bad.ctypes.data, t.shape[0], 2, C.byref(n), None)
+    assert rc == L.PKASP_EMESH
     rc = lib.pkasp_solve(None, None, None, 1, 1, None, None)
     assert rc == L.PKASP_EINVAL
     rc = lib.pkasp_solve_from_zero(None, None, None, 1, 1, None, None)
