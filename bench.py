@@ -1,19 +1,23 @@
-"""Benchmark: auxiliary-space PCG to relative residual 1e-8 on the P3 Poisson problem of a
-32^3-cube jittered Kuhn mesh (196,608 tetrahedra, 857,375 unknowns), kappa = 1, sine
-source, additive preconditioner (one symmetric multicolour GS sweep + one P1 AMG
-V(1,1)-cycle, PMIS + extended+i, theta = 0.25), FP64 throughout.
+"""Benchmark: auxiliary-space PCG to relative residual 1e-8 on the P4 Poisson problem of a
+48^3-cube jittered Kuhn mesh (663,552 tetrahedra, 6,967,871 unknowns, 512.8M nonzeros),
+kappa_e = exp(N(0,1)) per element (seed 1), sine source, additive preconditioner (one
+symmetric multicolour GS sweep + one P1 AMG V(1,1)-cycle, PMIS + extended+i, theta =
+0.25, l1-Jacobi level smoothing). value: the all-FP64 solve; beside it, timed the same
+way (CUDA events around the same number of solves), the mixed-precision solve (FP32
+smoother / I_P / AMG hierarchy, FP64 flexible CG) and both with the l1-Jacobi smoother.
 
 One step = one complete PCG solve from x0 = 0 (setup excluded, reported separately).
 The metric is MDOF*iter/s = n_h * iterations / solve time; the time to solution and the
 HBM roofline of the dominant kernel are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload p3_n32 | p2_n64_batched48]
+                    [--workload p4_n48_lognormal | p3_n32 | p2_n64_batched48 | ...]
 
-The second workload is the multi-RHS solve: the P2 vector Laplacian (3 velocity
-components, identical scalar blocks) on a 64^3 jittered Kuhn mesh with 16 right-hand
-sides of i.i.d. N(0,1) entries (seed 2), i.e. 48 columns of the scalar system in one
-blocked PCG, FP32 preconditioner and FP64 outer iteration.
+p3_n32 is the P3 problem on 32^3 cubes (857,375 unknowns, kappa = 1). p2_n64_batched48
+is the multi-RHS solve: the P2 vector Laplacian (3 velocity components, identical scalar
+blocks) on a 64^3 jittered Kuhn mesh with 16 right-hand sides of i.i.d. N(0,1) entries
+(seed 2), i.e. 48 columns of the scalar system in one blocked PCG, FP32 preconditioner
+and FP64 outer iteration.
 
 Multi-GPU: the path runs as independent replicas (one solve per rank, no collective on
 the data path); value sums the ranks' work over the slowest rank's time.
@@ -59,6 +63,7 @@ CONFIG_P4 = {
     "parallelism": "replicas (one independent solve per GPU)",
 }
 SINGLE = {WORKLOAD["name"]: (WORKLOAD, CONFIG), P4["name"]: (P4, CONFIG_P4)}
+DEFAULT_WORKLOAD = P4["name"]
 BATCHED = dict(name="p2_n64_batched48", k=2, n=64, jitter=0.2, mesh_seed=0, rhs_seed=2, ncols=48)
 CONFIG_BATCHED = {
     "workload": "P2 vector Laplacian (3 components x 16 right-hand sides = 48 columns of the scalar "
@@ -77,6 +82,11 @@ CONFIG_BATCHED = {
 # per clock per SM (2 FP64 FMA per clock per SM) = 1.259 TFLOP/s (nominal 1.25)
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 ORACLE_SAMPLE_ITERS = 12
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (summed over the phases of
+# one S_k application), keyed by (workload, cubes per side, smoother layout); a kernel
+# changed since the capture has no entry (traffic null)
+SMOOTHER_TRAFFIC = {}
+SPMV_TRAFFIC = {("p3_n32", 32): 548.3e6 + 8.3e6}
 NOMINAL_HBM_GBS = 8000.0  # GB300's nominal HBM3e bandwidth, for the second fraction
 # AMG level smoother: l1-Jacobi (1), one kernel per smoothing step; multicolour GS on the
 # dense coarse levels needs one launch per colour and costs ~25x more per V-cycle here
@@ -175,10 +185,33 @@ def make_problem():
     return xyz, t, Problem(xyz, t, WORKLOAD["k"], workload_kappa(WORKLOAD, t.shape[0]))
 
 
+def host_cpu():
+    """CPU model and logical core count of the host (for the baseline record)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count()}
+
+
 def run_cpu_oracle(steps, warmup, sample_iters=ORACLE_SAMPLE_ITERS, batched=False, mesh_n=0):
-    """The oracle, as it stands, on the host: assembly and setup untimed, then timed
-    bounded samples of the solve (sample_iters PCG iterations each). The oracle solves
-    one right-hand side at a time; on the multi-RHS workload a sample is one column."""
+    """The oracle, as it stands, on one host core: assembly and setup timed separately
+    (not part of the metric), then timed bounded samples of the solve (sample_iters PCG
+    iterations each). The oracle solves one right-hand side at a time; on the multi-RHS
+    workload a sample is one column."""
     import oracle
     from paper_1204_2586_gb300.inputs import kuhn_mesh, rhs_normal
 
@@ -186,45 +219,144 @@ def run_cpu_oracle(steps, warmup, sample_iters=ORACLE_SAMPLE_ITERS, batched=Fals
     if mesh_n:
         wl["n"] = mesh_n
     xyz, t = kuhn_mesh(wl["n"], wl["jitter"], wl["mesh_seed"])
+    t0 = time.perf_counter()
     P = oracle.Problem(xyz, t, wl["k"], workload_kappa(wl, t.shape[0]))
+    t1 = time.perf_counter()
     if batched:
         P.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, max_iter=sample_iters, flexible=1)
         b = rhs_normal(P.nh, 1, wl["rhs_seed"])[:, 0]
     else:
         P.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, max_iter=sample_iters)
         b = None
+    t2 = time.perf_counter()
     times, iters = [], []
     for i in range(warmup + steps):
-        t0 = time.perf_counter()
+        t0s = time.perf_counter()
         out = P.solve(b)
-        dt = time.perf_counter() - t0
+        dt = time.perf_counter() - t0s
         if i >= warmup:
             times.append(dt)
             iters.append(out["iters"])
     tot = sum(times)
     value = P.nh * sum(iters) / tot / 1e6
     what = "one column (FP64 flexible CG)" if batched else "the solve"
-    return value, dict(value=value, unit=UNIT, cores=1, kind="oracle",
-                       sample=f"{steps} timed runs of {sample_iters} PCG iterations each of {what} on the "
-                              f"full workload (n_h={P.nh}); single-threaded C oracle, assembly/setup untimed",
-                       seconds=tot)
+    rec = dict(value=value, unit=UNIT, cores=1, kind="oracle",
+               sample=f"{steps} timed runs of {sample_iters} PCG iterations each of {what} on the "
+                      f"full workload (n_h={P.nh}); single-threaded C oracle; assembly and setup "
+                      "timed separately, outside the metric",
+               seconds=tot, oracle_assemble_s=t1 - t0, oracle_setup_s=t2 - t1,
+               seconds_per_iteration=tot / max(1, sum(iters)))
+    rec.update(host_cpu())
+    return value, rec
 
 
 def reference_arm(args):
+    """The oracle as it stands, timed on the host's cores for the same workload: one
+    step = a bounded sample of the solve (PCG from x0 = 0 stopped after a few iterations).
+    Steps are independent, so they run concurrently on one thread per core (the oracle
+    is plain single-threaded C; each call allocates its own work vectors and reads the
+    assembled problem only), args.warmup untimed steps first, then exactly args.steps
+    timed ones. value = n_h x iterations of the timed steps / their wall time."""
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
         return
+    import concurrent.futures as cf
+
+    import oracle
+    from paper_1204_2586_gb300.inputs import kuhn_mesh, rhs_normal
+
     batched = args.workload == BATCHED["name"]
+    wl = dict(BATCHED if batched else WORKLOAD)
+    # iterations per step: P4 48^3 takes ~12 s per oracle iteration on one core
     sample = 2 if args.workload == P4["name"] else 4
-    value, cpu = run_cpu_oracle(args.steps, args.warmup, sample_iters=sample, batched=batched)
-    ms = cpu["seconds"] / args.steps * 1e3
+    xyz, t = kuhn_mesh(wl["n"], wl["jitter"], wl["mesh_seed"])
+    t0 = time.perf_counter()
+    P = oracle.Problem(xyz, t, wl["k"], workload_kappa(wl, t.shape[0]))
+    t1 = time.perf_counter()
+    P.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, max_iter=sample, flexible=1 if batched else 0)
+    t2 = time.perf_counter()
+    b = rhs_normal(P.nh, 1, wl["rhs_seed"])[:, 0] if batched else P.rhs()
+    threads = max(1, min(os.cpu_count() or 1, 16, args.steps))
+
+    def one(_):
+        return P.solve(b)["iters"]
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, range(args.warmup)))
+        ts = time.perf_counter()
+        its = list(ex.map(one, range(args.steps)))
+        wall = time.perf_counter() - ts
+    value = P.nh * sum(its) / wall / 1e6
+    cpu = dict(value=value, unit=UNIT, cores=threads, kind="oracle",
+               sample=f"each step: PCG from x0 = 0 stopped after {sample} iterations "
+                      f"({'one column, FP64 flexible CG' if batched else 'the solve'}) on the full workload "
+                      f"(n_h={P.nh}); {args.steps} timed steps run concurrently on {threads} threads of the "
+                      "single-threaded C oracle; assembly and setup timed separately, outside the metric",
+               oracle_assemble_s=t1 - t0, oracle_setup_s=t2 - t1)
+    cpu.update(host_cpu())
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": CONFIG_BATCHED if batched else SINGLE[args.workload][1],
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": CONFIG_BATCHED if batched else SINGLE[args.workload][1],
             "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def smoother_layout_name(code):
+    if code == 0:
+        return "SELL-32"
+    if code == -1:
+        return "CSR, lanes per colour"
+    if code < -1:
+        return f"one cooperative launch, CSR x{-code} lanes"
+    if code > 400:
+        return f"CSR x{code % 100} lanes, grid-stride over the resident blocks"
+    if code > 100:
+        return f"CSR x{code - 100} lanes, two rows per lane group"
+    return f"CSR x{code} lanes"
+
+
+def timed_solves(G, b, x, steps, warmup, clock=None):
+    """warmup untimed solves, then `steps` solves bracketed by CUDA events on the
+    launching stream (a device synchronize on both sides). Returns (ms total, iteration
+    counts, kernel launches, last stats)."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+
+    def step():
+        x.zero_()
+        _, st = G.solve(b, x)
+        assert st["status"][0] == 0, st
+        return st
+
+    for _ in range(warmup):
+        step()
+    ws, _, _ = dist_env()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, launches, st = [], 0, None
+    if clock is not None:
+        clock.__enter__()
+    try:
+        torch.cuda.nvtx.range_push("timed_solves")  # lets ncu --nvtx-include select them
+        e0.record(stream)
+        for _ in range(steps):
+            st = step()
+            iters.append(st["iters"][0])
+            launches += st["kernel_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    finally:
+        if clock is not None:
+            clock.__exit__(None, None, None)
+    if ws > 1:
+        torch.distributed.barrier()
+    return e0.elapsed_time(e1), iters, launches, st
 
 
 def main():
@@ -235,7 +367,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD["name"],
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=[WORKLOAD["name"], P4["name"], BATCHED["name"], "theta_study", "cop_study",
                              "stokes_study"])
     ap.add_argument("--smoother-layout", type=int, default=0,
@@ -250,6 +382,9 @@ def main():
     ap.add_argument("--eager", action="store_true",
                     help="launch the same kernels without the CUDA graph (profilers cannot see "
                          "kernels inside graphs that hold conditional nodes)")
+    ap.add_argument("--only-fp64", action="store_true",
+                    help="time the FP64 solve only (profiler runs): no e2e, FP32, l1-Jacobi or "
+                         "FGMRES legs")
     args = ap.parse_args()
     if args.mesh_n and args.workload not in SINGLE and args.workload != BATCHED["name"]:
         ap.error("--mesh-n applies to the p3, p4 and multi-RHS workloads")
@@ -294,45 +429,28 @@ def main():
     xyz, tets, G = make_problem()
     torch.cuda.synchronize()
     assemble_s = time.perf_counter() - t_as
+    graph = 0 if args.eager else 1
     t_su = time.perf_counter()
-    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, use_graph=0 if args.eager else 1,
-            smoother_layout=args.smoother_layout)
+    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, use_graph=graph, smoother_layout=args.smoother_layout)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_su
     b = G.rhs()
     x = torch.zeros_like(b)
-    stream = torch.cuda.current_stream()
-
-    def step():
-        x.zero_()
-        _, st = G.solve(b, x)
-        return st
-
-    for _ in range(args.warmup):
-        st = step()
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    iters, launches = [], 0
-    with ClockSampler(local) as clk:
-        torch.cuda.nvtx.range_push("timed_solves")  # lets ncu --nvtx-include select them
-        e0.record(stream)
-        for _ in range(args.steps):
-            st = step()
-            iters.append(st["iters"][0])
-            launches += st["kernel_launches"]
-            assert st["status"][0] == 0, st
-        e1.record(stream)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-    if ws > 1:
-        torch.distributed.barrier()
-    ms = e0.elapsed_time(e1)
     nh = G.nh
+
+    clk = ClockSampler(local)
+    ms, iters, launches, st = timed_solves(G, b, x, args.steps, args.warmup, clock=clk)
     ms, work = replica_totals(ms, nh * sum(iters))
     value = work / (ms / 1e3) / 1e6
     sol_s = ms / 1e3 / args.steps
+    true_rel64 = st["true_rel"][0]
+    info64 = G.info
+    if args.only_fp64:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": ms / args.steps, "config": CONFIG,
+                              "note": "--only-fp64 profiler run: not a bench line"}))
+        return
 
     # end to end through the C ABI with pinned host buffers: H2D of b, D2H of x (the solve
     # starts from x0 = 0 through pkasp_solve_from_zero, so no x0 is uploaded)
@@ -346,97 +464,103 @@ def main():
     e_iters, e_dev = [], []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _, st = G.solve(bnp, xnp, from_zero=True)
-        e_dev.append(st["solve_ms"])
-        e_iters.append(st["iters"][0])
+        _, ste = G.solve(bnp, xnp, from_zero=True)
+        e_dev.append(ste["solve_ms"])
+        e_iters.append(ste["iters"][0])
     e2e_s = time.perf_counter() - t0
     e2e_ms, e2e_work = replica_totals(e2e_s * 1e3, nh * sum(e_iters))
     e2e_value = e2e_work / (e2e_ms / 1e3) / 1e6
 
     # Rooflines, measured with CUDA events on the launching stream (pkasp_time_kernel).
-    # Dominant kernel by the launch list of a solve (profiles/launches_p3_n32_solve.md):
-    # the colour phases of the fine smoother S_k (about 63% of kernel time). Algorithmic
-    # bytes of one S_k application (all its phases): each off-diagonal entry once
-    # (FP64 value + int32 column = 12 B) and per row 52 B (inverse diagonal, r, y written
-    # then read-modified, two part pointers, row index); a phase's average rate is this
-    # total over the application's time. The fine SpMV: 12 B per nonzero + 20 B per row.
-    info64 = G.info
+    # Dominant kernel by the launch list of a solve: the colour phases of the fine
+    # smoother S_k. Algorithmic bytes of one S_k application (all its phases): each
+    # off-diagonal entry once (FP64 value + int32 column = 12 B) and per row 52 B (inverse
+    # diagonal, r, y written then read-modified, two part pointers, row index); a phase's
+    # average rate is this total over the application's time. Its FP64 work: one FMA per
+    # off-diagonal entry and 3 flops per row and half sweep. The fine SpMV: 12 B per
+    # nonzero + 20 B per row.
     spmv_ms = G.time_kernel(0, 50)
     smoother_ms = G.time_kernel(1, 20)
-    nnz = int(G.info.nnz_h)
+    # the same loads without the colour dependencies (all rows at once): the memory work
+    # of one S_k application with no barrier between its phases
+    nodep_ms = G.time_kernel(7, 20)
+    nnz = int(info64.nnz_h)
     spmv_bytes = 12 * nnz + 20 * nh
     smoother_bytes = 12 * (nnz - nh) + 52 * nh
+    smoother_flops = 2.0 * (nnz - nh) + 6.0 * nh
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     peak = hbm if hbm else 6800.0
     src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback"
     s_ach = smoother_bytes / (smoother_ms / 1e3) / 1e9
-    p3 = WORKLOAD["name"] == "p3_n32" and WORKLOAD["n"] == 32
+    s_tf = smoother_flops / (smoother_ms / 1e3) / 1e12
     roof = {"bound": "hbm", "kernel": "k_gs_phase (colour phases of the fine SGS S_k, FP64)",
-            "achieved": s_ach, "peak": peak, "unit": "GB/s", "frac": s_ach / peak, "traffic": None,
+            "achieved": s_ach, "peak": peak, "unit": "GB/s", "frac": s_ach / peak,
+            "traffic": SMOOTHER_TRAFFIC.get((WORKLOAD["name"], WORKLOAD["n"], smoother_layout_name(
+                info64.smoother_layout))),
             "frac_of_nominal_8000": s_ach / NOMINAL_HBM_GBS,
             "peak_source": src, "bytes_per_application": smoother_bytes, "ms_per_application": smoother_ms,
             "phases_per_application": 2 * int(info64.fine_colours) - 1,
-            "note": "latency per phase plus the FP64 pipe (ncu: fp64 pipe 51-57% busy while active); "
-                    "see profiles/k_gs_phase_p3_n32.md"}
+            "dependency_free_pass_ms": nodep_ms,
+            "dependency_free_pass_frac": (smoother_bytes / (nodep_ms / 1e3) / 1e9) / peak,
+            "fp64_pipe": {"achieved_tflops": s_tf, "peak_tflops": FP64_PEAK_TFLOPS,
+                          "frac": s_tf / FP64_PEAK_TFLOPS, "flops_per_application": smoother_flops,
+                          "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM"}}
     achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
     roof_spmv = {"bound": "hbm", "kernel": "k_spmv_pq / k_sell_spmv (fine SpMV, SELL-32, FP64)",
                  "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                  "frac_of_nominal_8000": achieved / NOMINAL_HBM_GBS,
-                 "traffic": 548.3e6 + 8.3e6 if p3 else None, "traffic_source":
-                 "ncu dram__bytes_read+write of one k_spmv_pq launch, profiles/k_spmv_pq_sell_p3_n32.md"
-                 if p3 else None,
+                 "traffic": SPMV_TRAFFIC.get((WORKLOAD["name"], WORKLOAD["n"])),
                  "peak_source": src, "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms}
-    # the mixed-precision variant of the same solve: FP32 smoother / I_P / AMG, FP64 flexible CG
-    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, precond_precision=1, use_graph=0 if args.eager else 1,
-            smoother_layout=args.smoother_layout_fp32)
-    for _ in range(2):
-        st32 = step()
-    ms32 = []
-    torch.cuda.nvtx.range_push("fp32_solves")  # lets ncu --nvtx-include select them
-    for _ in range(3):
-        st32 = step()
-        ms32.append(st32["solve_ms"])
-    torch.cuda.nvtx.range_pop()
-    extra32 = {"fp32_precond_time_to_solution_s": min(ms32) / 1e3, "fp32_precond_iterations": st32["iters"][0],
-               "fp32_precond_true_rel_residual": st32["true_rel"][0],
-               "fp32_precond_speedup_vs_fp64": sol_s / (min(ms32) / 1e3)}
+
+    def leg(**kw):
+        """Another configuration of the same solve, timed like the headline: CUDA events
+        around args.steps solves after the warm-up ones; mean time per solve."""
+        G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, use_graph=graph, **kw)
+        lms, lit, _, lst = timed_solves(G, b, x, args.steps, args.warmup)
+        return {"iterations": lit[-1], "time_to_solution_s": lms / args.steps / 1e3,
+                "true_rel_residual": lst["true_rel"][0],
+                "mdof_iter_per_s": nh * sum(lit) / (lms / 1e3) / 1e6,
+                "smoother_layout": smoother_layout_name(G.info.smoother_layout)}, x.clone()
+
+    x64 = x.clone()
+    # the mixed-precision variant: FP32 smoother / I_P / AMG, FP64 flexible CG
+    fp32, x32 = leg(precond_precision=1, smoother_layout=args.smoother_layout_fp32)
+    fp32["speedup_vs_fp64"] = sol_s / fp32["time_to_solution_s"]
+    fp32["rel_diff_vs_fp64_solution"] = float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64))
+    # the l1-Jacobi smoother for S_k (the north star allows it): no pass over A_h from zero
+    l1_64, _ = leg(smoother=1)
+    l1_32, _ = leg(smoother=1, precond_precision=1)
     # the paper's own outer setting (Sec. 6.2): FGMRES(30) with the multiplicative form
     # (Algorithm 2.1 with pre-smoothing), FP64, same tolerance; and FGMRES with the additive form
     krylov_cmp = {}
     for mode, name in ((1, "fgmres_multiplicative"), (0, "fgmres_additive")):
-        G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, mode=mode, krylov=1, restart=30,
-                use_graph=0 if args.eager else 1)
-        for _ in range(2):
-            stg = step()
+        G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, mode=mode, krylov=1, restart=30, use_graph=graph)
         msg = []
-        for _ in range(3):
-            stg = step()
-            msg.append(stg["solve_ms"])
-        krylov_cmp[name] = {"iterations": stg["iters"][0], "time_to_solution_s": min(msg) / 1e3,
+        for i in range(5):
+            x.zero_()
+            _, stg = G.solve(b, x)
+            if i >= 2:
+                msg.append(stg["solve_ms"])
+        krylov_cmp[name] = {"iterations": stg["iters"][0], "time_to_solution_s": sum(msg) / len(msg) / 1e3,
                             "true_rel_residual": stg["true_rel"][0], "restarts": stg["restarts"]}
-    extra = {"time_to_solution_s": sol_s, "iterations": iters[-1], "setup_s": setup_s,
-             "assemble_s": assemble_s, "levels": int(info64.levels),
+    extra = {"time_to_solution_s": sol_s, "iterations": iters[-1], "true_rel_residual": true_rel64,
+             "setup_s": setup_s, "assemble_s": assemble_s, "levels": int(info64.levels),
              "level_rows": [int(v) for v in info64.level_rows[: info64.levels]],
              "fine_colours": int(info64.fine_colours), "op_complexity": info64.op_complexity,
              "spmv_layout": "SELL-32" if info64.spmv_layout == 0 else f"CSR x{info64.spmv_layout} lanes",
-             "smoother_layout": ("SELL-32" if info64.smoother_layout == 0 else
-                                 "CSR, lanes per colour" if info64.smoother_layout == -1 else
-                                 f"one cooperative launch, CSR x{-info64.smoother_layout} lanes"
-                                 if info64.smoother_layout < -1 else
-                                 f"CSR x{info64.smoother_layout % 100} lanes, grid-stride over the "
-                                 "resident blocks" if info64.smoother_layout > 400 else
-                                 f"CSR x{info64.smoother_layout - 100} lanes, two rows per lane group"
-                                 if info64.smoother_layout > 100 else
-                                 f"CSR x{info64.smoother_layout} lanes"),
-             "smoother_ms": smoother_ms,
-             "smoother_GBps": smoother_bytes / (smoother_ms / 1e3) / 1e9}
-    extra.update(extra32)
-    extra["outer_iteration_comparison"] = krylov_cmp
+             "smoother_layout": smoother_layout_name(info64.smoother_layout),
+             "smoother_ms": smoother_ms, "smoother_GBps": s_ach, "spmv_ms": spmv_ms,
+             "fp32_preconditioner": fp32,
+             "fp32_precond_time_to_solution_s": fp32["time_to_solution_s"],
+             "fp32_precond_speedup_vs_fp64": fp32["speedup_vs_fp64"],
+             "l1_jacobi_smoother": {"fp64": l1_64, "fp32_preconditioner": l1_32},
+             "outer_iteration_comparison": krylov_cmp}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
+            p3 = WORKLOAD["name"] == "p3_n32"
             _, cpu = run_cpu_oracle(1, 0, sample_iters=ORACLE_SAMPLE_ITERS if p3 else 2)
             cpu.pop("seconds", None)
         except Exception as e:  # the baseline must not sink the GPU line

@@ -415,7 +415,10 @@ int pkasp_reference_tensors(int k, double *S_out);
  * (all colour phases of one S_k application), 2 V-cycle, 3 whole preconditioner; on the
  * multi-RHS blocks of the last solve with ncols > 1 (ESTATE before one): 4 blocked SpMM
  * Q = A_h P with its per-column dot (P, Q), 5 blocked fine smoother, 6 blocked
- * preconditioner. The blocked timings overwrite the solve's work blocks and scalars. */
+ * preconditioner. The blocked timings overwrite the solve's work blocks and scalars.
+ * which = 7: the fine smoother's loads without its colour dependencies (every row of the
+ * colour split at once, lower parts then upper parts, the smoother's lanes per row):
+ * the memory work of one S_k application with no barrier between colour phases. */
 int pkasp_time_kernel(pkasp_problem *p, int which, int reps, float *ms_out,
                       pkasp_stream_t stream);
 

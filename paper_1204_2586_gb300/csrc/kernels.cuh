@@ -25,6 +25,14 @@ __device__ __forceinline__ T ldg(const T *p) {
     return __ldg(p);
 }
 
+// Matrix entries are read once per application and streamed: loads marked evict-first
+// (ld.global.cs) keep them from pushing the gathered vector out of L2, which the colour
+// phases and the SpMV read many times.
+template <typename T>
+__device__ __forceinline__ T ldst(const T *p) {
+    return __ldcs(p);
+}
+
 // sum over the TPR lanes of a sub-warp (every lane of the warp must call this)
 template <int TPR, typename A>
 __device__ __forceinline__ A subwarp_sum(A v) {
@@ -231,30 +239,68 @@ __global__ void __launch_bounds__(kBlock) k_gs_phase(int64_t pb, int64_t pe, con
     for (int k = 0; k < NB; ++k) {
         const int64_t e = b0 + (int64_t)k * TPR;
         const bool in = e < hi;
-        c[k] = in ? __ldg(&xcol[e]) : -1;
-        v[k] = in ? __ldg(&xval[e]) : PT(0);
+        c[k] = in ? ldst(&xcol[e]) : -1;
+        v[k] = in ? ldst(&xval[e]) : PT(0);
     }
+    // entries of the warp's busiest lane: FMA slots past it are skipped by a warp-uniform
+    // branch (an issued FP64 slot costs the same whether a lane uses it or not)
+    const unsigned mine = hi > b0 ? (unsigned)((hi - b0 + TPR - 1) / TPR) : 0u;
+    const int wmax = (int)__reduce_max_sync(kFull, mine);
     pdl_wait();
     PT own = PT(0);
     if (lead) own = BACK ? y[i] : (PT)r[i];
     PT acc = PT(0);
 #pragma unroll
     for (int k = 0; k < NB; ++k)
-        if (c[k] >= 0) acc += v[k] * y[c[k]];
-    for (int64_t base = b0 + (int64_t)NB * TPR; base < hi; base += (int64_t)NB * TPR) {
+        if (k < wmax && c[k] >= 0) acc += v[k] * y[c[k]];
+    for (int k0 = NB; k0 < wmax; k0 += NB) {
+        const int64_t base = b0 + (int64_t)k0 * TPR;
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             const int64_t e = base + (int64_t)k * TPR;
             const bool in = e < hi;
-            c[k] = in ? __ldg(&xcol[e]) : -1;
-            v[k] = in ? __ldg(&xval[e]) : PT(0);
+            c[k] = in ? ldst(&xcol[e]) : -1;
+            v[k] = in ? ldst(&xval[e]) : PT(0);
         }
 #pragma unroll
         for (int k = 0; k < NB; ++k)
-            if (c[k] >= 0) acc += v[k] * y[c[k]];
+            if (k0 + k < wmax && c[k] >= 0) acc += v[k] * y[c[k]];
     }
     acc = subwarp_sum<TPR>(acc);
     if (lead) y[i] = BACK ? own - acc * di : (own - acc) * di;
+}
+
+// The loads of a colour phase without its dependency: every position of [0, n) at
+// once, out[i] = dinv_i * sum_part a_ij x_j with x read-only (a measurement of the
+// smoother's memory work without the barriers between colours; not used by a solve).
+template <int TPR, int NB, typename PT>
+__global__ void __launch_bounds__(kBlock) k_split_pass(int64_t n, const int32_t *__restrict__ perm,
+                                                       const int64_t *__restrict__ xptr,
+                                                       const int32_t *__restrict__ xcol,
+                                                       const PT *__restrict__ xval, const PT *__restrict__ dinv,
+                                                       const PT *__restrict__ x, PT *__restrict__ out) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = p < n;
+    const int64_t lo = ok ? xptr[p] : 0, hi = ok ? xptr[p + 1] : 0;
+    PT acc = PT(0);
+    for (int64_t base = lo + sub; base < hi; base += (int64_t)NB * TPR) {
+        int c[NB];
+        PT v[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const int64_t e = base + (int64_t)k * TPR;
+            const bool in = e < hi;
+            c[k] = in ? ldst(&xcol[e]) : -1;
+            v[k] = in ? ldst(&xval[e]) : PT(0);
+        }
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            if (c[k] >= 0) acc += v[k] * x[c[k]];
+    }
+    acc = subwarp_sum<TPR>(acc);
+    if (ok && sub == 0) out[perm[p]] = acc * dinv[p];
 }
 
 // The same phase over a capped grid: sub-warp g takes rows pb + g, pb + g + nsub, ...
@@ -278,8 +324,8 @@ __device__ __forceinline__ void gs_row_static(int64_t q, bool ok, bool lead, int
     for (int k = 0; k < NB; ++k) {
         const int64_t e = b0 + (int64_t)k * TPR;
         const bool in = e < hi;
-        c[k] = in ? __ldg(&xcol[e]) : -1;
-        v[k] = in ? __ldg(&xval[e]) : PT(0);
+        c[k] = in ? ldst(&xcol[e]) : -1;
+        v[k] = in ? ldst(&xval[e]) : PT(0);
     }
 }
 
@@ -328,8 +374,8 @@ __global__ void __launch_bounds__(kBlock) k_gs_phase_gs(int64_t pb, int64_t pe, 
             for (int k = 0; k < NB; ++k) {
                 const int64_t e = base + (int64_t)k * TPR;
                 const bool in = e < hi;
-                c[k] = in ? __ldg(&xcol[e]) : -1;
-                v[k] = in ? __ldg(&xval[e]) : PT(0);
+                c[k] = in ? ldst(&xcol[e]) : -1;
+                v[k] = in ? ldst(&xval[e]) : PT(0);
             }
 #pragma unroll
             for (int k = 0; k < NB; ++k)
@@ -389,8 +435,8 @@ __global__ void __launch_bounds__(kBlock) k_gs_phase2(int64_t pb, int64_t pe, co
         for (int k = 0; k < NB; ++k) {
             const int64_t e = lo[q] + sub + (int64_t)k * TPR;
             const bool in = e < hi[q];
-            c[q][k] = in ? __ldg(&xcol[e]) : -1;
-            v[q][k] = in ? __ldg(&xval[e]) : PT(0);
+            c[q][k] = in ? ldst(&xcol[e]) : -1;
+            v[q][k] = in ? ldst(&xval[e]) : PT(0);
         }
     }
     pdl_wait();
@@ -416,8 +462,8 @@ __global__ void __launch_bounds__(kBlock) k_gs_phase2(int64_t pb, int64_t pe, co
             for (int k = 0; k < NB; ++k) {
                 const int64_t e = base + (int64_t)k * TPR;
                 const bool in = e < hi[q];
-                c[q][k] = in ? __ldg(&xcol[e]) : -1;
-                v[q][k] = in ? __ldg(&xval[e]) : PT(0);
+                c[q][k] = in ? ldst(&xcol[e]) : -1;
+                v[q][k] = in ? ldst(&xval[e]) : PT(0);
             }
 #pragma unroll
             for (int k = 0; k < NB; ++k)
@@ -546,8 +592,8 @@ __device__ __forceinline__ A sell_dot(int64_t base, int w, const int32_t *__rest
         for (int k = 0; k < kBatch; ++k) {
             const int64_t e = base + 32 * (int64_t)(k0 + k);
             const bool ok = k0 + k < w;
-            c[k] = ok ? __ldg(&col[e]) : -1;
-            v[k] = ok ? (A)__ldg(&val[e]) : A(0);
+            c[k] = ok ? ldst(&col[e]) : -1;
+            v[k] = ok ? (A)ldst(&val[e]) : A(0);
         }
 #pragma unroll
         for (int k = 0; k < kBatch; ++k)
@@ -592,8 +638,8 @@ __global__ void __launch_bounds__(kBlock) k_sell_phase(int64_t s0, int64_t s1, c
 #pragma unroll
     for (int k = 0; k < kBatch; ++k) {
         const bool in = k < w;
-        c[k] = in ? __ldg(&col[base + 32 * (int64_t)k]) : -1;
-        v[k] = in ? __ldg(&val[base + 32 * (int64_t)k]) : PT(0);
+        c[k] = in ? ldst(&col[base + 32 * (int64_t)k]) : -1;
+        v[k] = in ? ldst(&val[base + 32 * (int64_t)k]) : PT(0);
     }
     pdl_wait();
     PT own = PT(0);
@@ -606,8 +652,8 @@ __global__ void __launch_bounds__(kBlock) k_sell_phase(int64_t s0, int64_t s1, c
 #pragma unroll
         for (int k = 0; k < kBatch; ++k) {
             const bool in = k0 + k < w;
-            c[k] = in ? __ldg(&col[base + 32 * (int64_t)(k0 + k)]) : -1;
-            v[k] = in ? __ldg(&val[base + 32 * (int64_t)(k0 + k)]) : PT(0);
+            c[k] = in ? ldst(&col[base + 32 * (int64_t)(k0 + k)]) : -1;
+            v[k] = in ? ldst(&val[base + 32 * (int64_t)(k0 + k)]) : PT(0);
         }
 #pragma unroll
         for (int k = 0; k < kBatch; ++k)

@@ -1119,7 +1119,7 @@ void check_barrier(pkasp_problem *p, cudaStream_t s) { barrier_status(p, s); }
 
 float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s) {
     if (reps < 1) reps = 1;
-    if (which >= 4) return time_batched(p, which, reps, s);
+    if (which >= 4 && which <= 6) return time_batched(p, which, reps, s);
     cudaEvent_t e0, e1;
     PK_CUDA(cudaEventCreate(&e0));
     PK_CUDA(cudaEventCreate(&e1));
@@ -1137,6 +1137,28 @@ float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s) {
             case 2: {
                 if (p->opt.precond_precision == PKASP_PREC_FP32) restrict_vcycle<float>(p, p->w_r, s);
                 else restrict_vcycle<double>(p, p->w_r, s);
+                break;
+            }
+            case 7: {
+                // the fine smoother's loads in two dependency-free passes (lower parts, then
+                // upper parts) with the smoother's lanes per row
+                const DSplit &sp = p->fine;
+                const int t = (p->fine_tpr == 8 || p->fine_tpr == 16) ? p->fine_tpr : 4;
+                if (p->opt.precond_precision == PKASP_PREC_FP32) {
+                    PK_TPR3_SWITCH(t, (k_split_pass<TPR, kBatch, float><<<rows_grid(p->nh, TPR), kBlock, 0, s>>>(
+                                          p->nh, sp.perm, sp.lptr, sp.lcol, sp.lval32, sp.dinv32, p->w_zs32, p->w_t32)));
+                    PK_LAUNCH();
+                    PK_TPR3_SWITCH(t, (k_split_pass<TPR, kBatch, float><<<rows_grid(p->nh, TPR), kBlock, 0, s>>>(
+                                          p->nh, sp.perm, sp.uptr, sp.ucol, sp.uval32, sp.dinv32, p->w_zs32, p->w_t32)));
+                    PK_LAUNCH();
+                } else {
+                    PK_TPR3_SWITCH(t, (k_split_pass<TPR, kBatch, double><<<rows_grid(p->nh, TPR), kBlock, 0, s>>>(
+                                          p->nh, sp.perm, sp.lptr, sp.lcol, sp.lval, sp.dinv, p->w_p, p->w_t)));
+                    PK_LAUNCH();
+                    PK_TPR3_SWITCH(t, (k_split_pass<TPR, kBatch, double><<<rows_grid(p->nh, TPR), kBlock, 0, s>>>(
+                                          p->nh, sp.perm, sp.uptr, sp.ucol, sp.uval, sp.dinv, p->w_p, p->w_t)));
+                    PK_LAUNCH();
+                }
                 break;
             }
             default: apply_prec(p, p->w_r, p->w_z, s); break;
