@@ -85,8 +85,8 @@ ORACLE_SAMPLE_ITERS = 12
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (summed over the phases of
 # one S_k application), keyed by (workload, cubes per side, smoother layout); a kernel
 # changed since the capture has no entry (traffic null)
-SMOOTHER_TRAFFIC = {}
-SPMV_TRAFFIC = {("p3_n32", 32): 548.3e6 + 8.3e6}
+SMOOTHER_TRAFFIC = {("p4_n48_lognormal", 48, "CSR x4 lanes"): 11.308e9}
+SPMV_TRAFFIC = {("p4_n48_lognormal", 48): (6843780864 + 81747712 + 6830649600 + 90946816 + 6830844928 + 90865664) / 3}
 NOMINAL_HBM_GBS = 8000.0  # GB300's nominal HBM3e bandwidth, for the second fraction
 # AMG level smoother: l1-Jacobi (1), one kernel per smoothing step; multicolour GS on the
 # dense coarse levels needs one launch per colour and costs ~25x more per V-cycle here
@@ -484,6 +484,10 @@ def main():
     # the same loads without the colour dependencies (all rows at once): the memory work
     # of one S_k application with no barrier between its phases
     nodep_ms = G.time_kernel(7, 20)
+    # the GPU's random 8-byte gather rate from a vector of n_h values (pkasp_time_kernel
+    # mode 8 returns nanoseconds per gather): the colour phases gather one value per
+    # off-diagonal entry, and their L2 sector traffic, not DRAM bytes, binds them
+    gather_ns = G.time_kernel(8, 5)
     nnz = int(info64.nnz_h)
     spmv_bytes = 12 * nnz + 20 * nh
     smoother_bytes = 12 * (nnz - nh) + 52 * nh
@@ -498,10 +502,17 @@ def main():
             "achieved": s_ach, "peak": peak, "unit": "GB/s", "frac": s_ach / peak,
             "traffic": SMOOTHER_TRAFFIC.get((WORKLOAD["name"], WORKLOAD["n"], smoother_layout_name(
                 info64.smoother_layout))),
+            "traffic_note": "ncu dram__bytes_read+write summed over the 81 launches of one application, "
+                            "profiles/k_gs_phase_p4_n48.md",
             "frac_of_nominal_8000": s_ach / NOMINAL_HBM_GBS,
             "peak_source": src, "bytes_per_application": smoother_bytes, "ms_per_application": smoother_ms,
             "phases_per_application": 2 * int(info64.fine_colours) - 1,
             "dependency_free_pass_ms": nodep_ms,
+            "gather_roof": {"achieved_Ggathers_per_s": (nnz - nh) / (smoother_ms / 1e3) / 1e9,
+                            "peak_Ggathers_per_s": 1.0 / gather_ns,
+                            "frac": (nnz - nh) / (smoother_ms / 1e3) / 1e9 * gather_ns,
+                            "peak_source": "measured live: random 8-byte gathers from an n_h vector "
+                                           "(pkasp_time_kernel mode 8)"},
             "dependency_free_pass_frac": (smoother_bytes / (nodep_ms / 1e3) / 1e9) / peak,
             "fp64_pipe": {"achieved_tflops": s_tf, "peak_tflops": FP64_PEAK_TFLOPS,
                           "frac": s_tf / FP64_PEAK_TFLOPS, "flops_per_application": smoother_flops,
@@ -511,6 +522,7 @@ def main():
                  "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                  "frac_of_nominal_8000": achieved / NOMINAL_HBM_GBS,
                  "traffic": SPMV_TRAFFIC.get((WORKLOAD["name"], WORKLOAD["n"])),
+                 "traffic_note": "ncu dram__bytes_read+write per launch (mean of 3), profiles/k_spmv_pq_p4_n48.md",
                  "peak_source": src, "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms}
 
     def leg(**kw):

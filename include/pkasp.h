@@ -418,7 +418,11 @@ int pkasp_reference_tensors(int k, double *S_out);
  * preconditioner. The blocked timings overwrite the solve's work blocks and scalars.
  * which = 7: the fine smoother's loads without its colour dependencies (every row of the
  * colour split at once, lower parts then upper parts, the smoother's lanes per row):
- * the memory work of one S_k application with no barrier between colour phases. */
+ * the memory work of one S_k application with no barrier between colour phases.
+ * which = 8: a gather-rate probe, random 8-byte gathers from an n_h vector driven by a
+ * streamed index array of min(64M, 8 n_h) entries (scratch allocated for the call);
+ * *ms_out then receives NANOSECONDS PER GATHER, the inverse of the GPU's random gather
+ * rate from a vector of the size the smoother gathers from. */
 int pkasp_time_kernel(pkasp_problem *p, int which, int reps, float *ms_out,
                       pkasp_stream_t stream);
 

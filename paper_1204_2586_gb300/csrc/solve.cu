@@ -1117,12 +1117,53 @@ int solve_device(pkasp_problem *p, const double *b, double *x, int ncols, int64_
 
 void check_barrier(pkasp_problem *p, cudaStream_t s) { barrier_status(p, s); }
 
+namespace {
+// Gather-rate probe: random 8-byte gathers x[idx[j]] driven by a streamed index array,
+// eight independent gathers in flight per thread (the access pattern of a sparse row's
+// columns without its locality). Not used by a solve.
+__global__ void __launch_bounds__(kBlock) k_gather_probe(int64_t m, const int32_t *__restrict__ idx,
+                                                         const double *__restrict__ x, double *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = t; i + 7 * st < m; i += 8 * st) {
+        int c[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[k] = ldst(&idx[i + k * st]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] += x[c[k]];
+    }
+    double z = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) z += s[k];
+    if (z == -1.0) out[0] = z;  // keeps the loads; x is never -1 in a probe
+}
+
+// idx[j] = a SplitMix64 hash of j modulo n (the probe's random columns)
+__global__ void k_probe_indices(int64_t m, int64_t n, int32_t *__restrict__ idx) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    uint64_t z = 0x5EEDull + ((uint64_t)j + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    idx[j] = (int32_t)(z % (uint64_t)n);
+}
+
+}  // namespace
+
 float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s) {
     if (reps < 1) reps = 1;
     if (which >= 4 && which <= 6) return time_batched(p, which, reps, s);
     cudaEvent_t e0, e1;
     PK_CUDA(cudaEventCreate(&e0));
     PK_CUDA(cudaEventCreate(&e1));
+    int32_t *probe_idx = nullptr;
+    const int64_t probe_m = std::min<int64_t>(64ll << 20, 8 * std::max<int64_t>(p->nh, 1));
+    if (which == 8) {
+        PK_CUDA(cudaMallocAsync((void **)&probe_idx, sizeof(int32_t) * probe_m, s));
+        k_probe_indices<<<(unsigned)((probe_m + kBlock - 1) / kBlock), kBlock, 0, s>>>(probe_m, p->nh, probe_idx);
+        PK_LAUNCH();
+    }
     // inputs: r = f_h in w_r, p-vector = f_h
     PK_CUDA(cudaMemcpyAsync(p->w_r, p->d_b, sizeof(double) * p->nh, cudaMemcpyDeviceToDevice, s));
     PK_CUDA(cudaMemcpyAsync(p->w_p, p->d_b, sizeof(double) * p->nh, cudaMemcpyDeviceToDevice, s));
@@ -1161,6 +1202,11 @@ float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s) {
                 }
                 break;
             }
+            case 8:
+                // random 8-byte gathers from an n_h vector (f_h) by a streamed index array
+                k_gather_probe<<<kRedGrid * 4, kBlock, 0, s>>>(probe_m, probe_idx, p->w_p, p->w_t);
+                PK_LAUNCH();
+                break;
             default: apply_prec(p, p->w_r, p->w_z, s); break;
         }
     };
@@ -1173,6 +1219,12 @@ float time_kernel(pkasp_problem *p, int which, int reps, cudaStream_t s) {
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (probe_idx) {
+        PK_CUDA(cudaFreeAsync(probe_idx, s));
+        PK_CUDA(cudaStreamSynchronize(s));
+    }
+    // mode 8 reports nanoseconds per gather instead of milliseconds per launch
+    if (which == 8) return ms / reps * 1e6f / (float)probe_m;
     return ms / reps;
 }
 
