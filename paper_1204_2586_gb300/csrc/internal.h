@@ -292,9 +292,20 @@ float time_batched(pkasp_problem *p, int which, int reps, cudaStream_t s);
 // FGMRES(m) outer iteration (gmres.cu); b and x device vectors [n_h]
 int solve_gmres(pkasp_problem *p, const double *b, double *x, pkasp_stats *st, cudaStream_t s);
 void free_gmres(pkasp_problem *p);
-// Stokes (stokes.cpp: host assembly of B = -div_h, B^T and the pressure mass matrix;
-// stokes.cu: operator, block preconditioner, FGMRES)
-void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t &np);
+// Stokes (stokes.cpp: patterns of B = -div_h, B^T and the pressure mass matrix, and
+// their host values for the host-only entry point; stokes.cu: device assembly of the
+// values, operator, block preconditioner, FGMRES)
+struct StokesPattern {
+    int64_t np = 0;
+    int nu = 0, npl = 0;                 // local velocity / pressure nodes
+    std::vector<int32_t> elem_p;         // [nt][npl] pressure node of each local node
+    std::vector<double> R, Mr;           // reference tensors [4][npl][nu], [npl][npl]
+    std::vector<int64_t> iptr, ient;     // pressure node -> (element * 64 + local)
+    HCSR B, BT, M;                       // patterns (values empty)
+    std::vector<int64_t> bt_src;         // B^T entry o copies B entry bt_src[o]
+};
+void stokes_patterns(int k, int64_t nv, int64_t nt, const double *xyz, const int32_t *tets, int64_t nh,
+                     const int32_t *elem_dof, StokesPattern &P);
 // the same from a mesh and its P_k unknown map (elem_dof[nt][nloc(k)]), host only
 void stokes_blocks(int k, int64_t nv, int64_t nt, const double *xyz, const int32_t *tets, int64_t nh,
                    const int32_t *elem_dof, HCSR &B, HCSR &BT, HCSR &M, int64_t &np);

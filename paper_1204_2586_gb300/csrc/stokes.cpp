@@ -1,9 +1,10 @@
-// stokes.cpp -- host assembly of the Taylor-Hood P_k - P_{k-1} Stokes blocks (Sec. 5):
+// stokes.cpp -- host part of the Taylor-Hood P_k - P_{k-1} Stokes blocks (Sec. 5):
 // B = -div_h (rows: the P_{k-1} pressure nodes, all of them; columns: the velocity
 // unknowns, component-major c n_h + j), its transpose and the pressure mass matrix M_p.
-// One-off setup work, like the DOF map: the element integrals come from reference
-// tensors computed once by Grundmann-Moeller quadrature, and every row sums its
-// elements in ascending element order (rows in parallel).
+// Like the DOF map and the A_h pattern, the patterns and the reference tensors are built
+// here (one-off setup work); pkasp_stokes_setup assembles the values on the device
+// (stokes.cu). The host values below serve the host-only entry point. Every row sums its
+// elements in ascending element order.
 #include <algorithm>
 #include <cmath>
 #include <thread>
@@ -91,23 +92,32 @@ void node_incidence(int64_t nnodes, int64_t nt, int nl, const std::vector<int32_
 
 }  // namespace
 
-void stokes_blocks(int k, int64_t nv, int64_t nt, const double *xyz, const int32_t *tets, int64_t nh,
-                   const int32_t *elem_dof, HCSR &B, HCSR &BT, HCSR &M, int64_t &np) {
+// Patterns and reference data of the Taylor-Hood blocks: the pressure DOF map (degree
+// k-1, no Dirichlet removal), the reference tensors R[a][m][n] = (1/|T|) int psi_m
+// dphi_n/dlambda_a and Mr[m][r] = (1/|T|) int psi_m psi_r by Grundmann-Moeller quadrature
+// (exact to degree 2(k-1)+1), the incidence pressure node -> (element, local) with
+// elements ascending, the sorted column patterns of B and M_p per pressure row, and the
+// pattern of B^T with the B entry each of its entries copies (bt_src).
+void stokes_patterns(int k, int64_t nv, int64_t nt, const double *xyz, const int32_t *tets, int64_t nh,
+                     const int32_t *elem_dof, StokesPattern &P) {
     const int kp = k - 1;
     const int nu = nloc_of(k), npl = nloc_of(kp);
+    P.nu = nu;
+    P.npl = npl;
     HostMesh hm{kp, nv, nt, xyz, tets};
     DofMap Dp;
     build_dofmap(hm, Dp);
-    np = Dp.n_all;
-    // reference tensors by quadrature: R[a][m][n] = (1/|T|) int psi_m dphi_n/dlambda_a,
-    // Mr[m][q] = (1/|T|) int psi_m psi_q (the rule is exact to degree 2(k-1)+1)
+    const int64_t np = Dp.n_all;
+    P.np = np;
+    P.elem_p = Dp.elem_all;
     std::vector<double> lam, w;
     gm_rule(std::max(kp, 1), lam, w);
     const int nq = (int)w.size();
     std::vector<int> mu, mp;
     ref_nodes(k, mu);
     ref_nodes(kp, mp);
-    std::vector<double> R((size_t)4 * npl * nu, 0.0), Mr((size_t)npl * npl, 0.0);
+    P.R.assign((size_t)4 * npl * nu, 0.0);
+    P.Mr.assign((size_t)npl * npl, 0.0);
     std::vector<double> psi(npl), dphi((size_t)4 * nu);
     for (int q = 0; q < nq; ++q) {
         const double *l = &lam[4 * q];
@@ -124,23 +134,12 @@ void stokes_blocks(int k, int64_t nv, int64_t nt, const double *xyz, const int32
         }
         for (int a = 0; a < 4; ++a)
             for (int m = 0; m < npl; ++m)
-                for (int n = 0; n < nu; ++n) R[((size_t)a * npl + m) * nu + n] += 6.0 * w[q] * psi[m] * dphi[a * nu + n];
+                for (int n = 0; n < nu; ++n) P.R[((size_t)a * npl + m) * nu + n] += 6.0 * w[q] * psi[m] * dphi[a * nu + n];
         for (int m = 0; m < npl; ++m)
-            for (int r = 0; r < npl; ++r) Mr[(size_t)m * npl + r] += 6.0 * w[q] * psi[m] * psi[r];
+            for (int r = 0; r < npl; ++r) P.Mr[(size_t)m * npl + r] += 6.0 * w[q] * psi[m] * psi[r];
     }
-    // element geometry
-    std::vector<double> grads((size_t)nt * 12), vols(nt);
-    for (int64_t t = 0; t < nt; ++t) {
-        double X[12], g[4][3];
-        for (int v = 0; v < 4; ++v)
-            for (int c = 0; c < 3; ++c) X[3 * v + c] = xyz[3 * (int64_t)tets[4 * t + v] + c];
-        vols[t] = tet_gradients(X, g);
-        for (int a = 0; a < 4; ++a)
-            for (int c = 0; c < 3; ++c) grads[t * 12 + a * 3 + c] = g[a][c];
-    }
-    std::vector<int64_t> iptr, ient;
-    node_incidence(np, nt, npl, Dp.elem_all, iptr, ient);
-    // pattern per pressure row: sorted unique columns
+    node_incidence(np, nt, npl, Dp.elem_all, P.iptr, P.ient);
+    HCSR &B = P.B, &M = P.M, &BT = P.BT;
     B.n = np;
     B.m = 3 * nh;
     M.n = np;
@@ -153,8 +152,8 @@ void stokes_blocks(int k, int64_t nv, int64_t nt, const double *xyz, const int32
         for (int64_t q = b; q < e; ++q) {
             bc.clear();
             mc.clear();
-            for (int64_t x = iptr[q]; x < iptr[q + 1]; ++x) {
-                const int64_t t = ient[x] / 64;
+            for (int64_t x = P.iptr[q]; x < P.iptr[q + 1]; ++x) {
+                const int64_t t = P.ient[x] / 64;
                 for (int n = 0; n < nu; ++n) {
                     const int32_t j = elem_dof[t * nu + n];
                     if (j < 0) continue;
@@ -175,37 +174,11 @@ void stokes_blocks(int k, int64_t nv, int64_t nt, const double *xyz, const int32
         M.ptr[q + 1] = M.ptr[q] + (int64_t)mcols[q].size();
     }
     B.col.resize(B.ptr[np]);
-    B.val.assign(B.ptr[np], 0.0);
     M.col.resize(M.ptr[np]);
-    M.val.assign(M.ptr[np], 0.0);
     rows_parallel(np, [&](int64_t b, int64_t e) {
         for (int64_t q = b; q < e; ++q) {
             std::copy(bcols[q].begin(), bcols[q].end(), B.col.begin() + B.ptr[q]);
             std::copy(mcols[q].begin(), mcols[q].end(), M.col.begin() + M.ptr[q]);
-            const int32_t *bcb = &B.col[B.ptr[q]], *bce = bcb + bcols[q].size();
-            const int32_t *mcb = &M.col[M.ptr[q]], *mce = mcb + mcols[q].size();
-            for (int64_t x = iptr[q]; x < iptr[q + 1]; ++x) {
-                const int64_t t = ient[x] / 64;
-                const int m = (int)(ient[x] % 64);
-                const double vol = vols[t];
-                const double *g = &grads[t * 12];
-                for (int n = 0; n < nu; ++n) {
-                    const int32_t j = elem_dof[t * nu + n];
-                    if (j < 0) continue;
-                    for (int c = 0; c < 3; ++c) {
-                        double s = 0.0;
-                        for (int a = 0; a < 4; ++a) s += g[a * 3 + c] * R[((size_t)a * npl + m) * nu + n];
-                        const int32_t col = (int32_t)(c * nh + j);
-                        const int64_t pos = std::lower_bound(bcb, bce, col) - bcb;
-                        B.val[B.ptr[q] + pos] += -vol * s;
-                    }
-                }
-                for (int r = 0; r < npl; ++r) {
-                    const int32_t col = Dp.elem_all[t * npl + r];
-                    const int64_t pos = std::lower_bound(mcb, mce, col) - mcb;
-                    M.val[M.ptr[q] + pos] += vol * Mr[(size_t)m * npl + r];
-                }
-            }
         }
     });
     // B^T: columns of B become rows, entries in ascending pressure row
@@ -215,18 +188,70 @@ void stokes_blocks(int k, int64_t nv, int64_t nt, const double *xyz, const int32
     for (int64_t x = 0; x < B.ptr[np]; ++x) BT.ptr[B.col[x] + 1]++;
     for (int64_t i = 0; i < BT.n; ++i) BT.ptr[i + 1] += BT.ptr[i];
     BT.col.resize(B.ptr[np]);
-    BT.val.resize(B.ptr[np]);
+    P.bt_src.resize(B.ptr[np]);
     std::vector<int64_t> fill(BT.ptr.begin(), BT.ptr.end() - 1);
     for (int64_t q = 0; q < np; ++q)
         for (int64_t x = B.ptr[q]; x < B.ptr[q + 1]; ++x) {
             const int64_t o = fill[B.col[x]]++;
             BT.col[o] = (int32_t)q;
-            BT.val[o] = B.val[x];
+            P.bt_src[o] = x;
         }
 }
 
-void stokes_assemble(const pkasp_problem *p, HCSR &B, HCSR &BT, HCSR &M, int64_t &np) {
-    stokes_blocks(p->k, p->nv, p->nt, p->xyz.data(), p->tets.data(), p->nh, p->elem_dof.data(), B, BT, M, np);
+// Host values of the blocks (the host-only entry point; pkasp_stokes_setup assembles the
+// same values on the device): every pressure row sums its elements in ascending order.
+void stokes_blocks(int k, int64_t nv, int64_t nt, const double *xyz, const int32_t *tets, int64_t nh,
+                   const int32_t *elem_dof, HCSR &B, HCSR &BT, HCSR &M, int64_t &np) {
+    StokesPattern P;
+    stokes_patterns(k, nv, nt, xyz, tets, nh, elem_dof, P);
+    np = P.np;
+    const int nu = P.nu, npl = P.npl;
+    std::vector<double> grads((size_t)nt * 12), vols(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        double X[12], g[4][3];
+        for (int v = 0; v < 4; ++v)
+            for (int c = 0; c < 3; ++c) X[3 * v + c] = xyz[3 * (int64_t)tets[4 * t + v] + c];
+        vols[t] = tet_gradients(X, g);
+        for (int a = 0; a < 4; ++a)
+            for (int c = 0; c < 3; ++c) grads[t * 12 + a * 3 + c] = g[a][c];
+    }
+    B = std::move(P.B);
+    M = std::move(P.M);
+    BT = std::move(P.BT);
+    B.val.assign(B.col.size(), 0.0);
+    M.val.assign(M.col.size(), 0.0);
+    rows_parallel(np, [&](int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; ++q) {
+            const int32_t *bcb = &B.col[B.ptr[q]], *bce = bcb + (B.ptr[q + 1] - B.ptr[q]);
+            const int32_t *mcb = &M.col[M.ptr[q]], *mce = mcb + (M.ptr[q + 1] - M.ptr[q]);
+            for (int64_t x = P.iptr[q]; x < P.iptr[q + 1]; ++x) {
+                const int64_t t = P.ient[x] / 64;
+                const int m = (int)(P.ient[x] % 64);
+                const double vol = vols[t];
+                const double *g = &grads[t * 12];
+                for (int n = 0; n < nu; ++n) {
+                    const int32_t j = elem_dof[t * nu + n];
+                    if (j < 0) continue;
+                    for (int c = 0; c < 3; ++c) {
+                        double s = 0.0;
+                        for (int a = 0; a < 4; ++a) s += g[a * 3 + c] * P.R[((size_t)a * npl + m) * nu + n];
+                        const int32_t col = (int32_t)(c * nh + j);
+                        const int64_t pos = std::lower_bound(bcb, bce, col) - bcb;
+                        B.val[B.ptr[q] + pos] += -vol * s;
+                    }
+                }
+                for (int r = 0; r < npl; ++r) {
+                    const int32_t col = P.elem_p[t * npl + r];
+                    const int64_t pos = std::lower_bound(mcb, mce, col) - mcb;
+                    M.val[M.ptr[q] + pos] += vol * P.Mr[(size_t)m * npl + r];
+                }
+            }
+        }
+    });
+    BT.val.resize(BT.col.size());
+    for (size_t o = 0; o < BT.val.size(); ++o) BT.val[o] = B.val[P.bt_src[o]];
 }
+
+
 
 }  // namespace pk

@@ -1,6 +1,7 @@
 // stokes.cu -- the Taylor-Hood P_k - P_{k-1} Stokes system of Sec. 5 on the device:
 //   F = [A B^T; B 0], A = three copies of the Dirichlet P_k Laplacian A_h (velocity
-//   unknowns component-major), B = -div_h (stokes.cpp assembles it), and the block upper
+//   unknowns component-major), B = -div_h (patterns from stokes.cpp, values assembled
+//   here), and the block upper
 //   triangular preconditioner Q_t = [A B^T; 0 -S]^{-1} of Eq. (5.4) with
 //     z_p = -M_p^{-1} r_p   (mp_iters steps of CG with the diagonal of M_p, from zero)
 //     z_u = B_aux (r_u - B^T z_p)   (the auxiliary-space preconditioner per component),
@@ -44,6 +45,102 @@ struct StokesWork {
 namespace {
 
 __device__ __forceinline__ bool gated_off(const int *gate) { return gate != nullptr && *gate == 0; }
+
+// first position in col[lo, hi) (ascending) holding a value >= j
+__device__ __forceinline__ int64_t ks_lower_bound(const int32_t *col, int64_t lo, int64_t hi, int32_t j) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < j) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Values of B = -div_h and M_p, one warp per pressure row q: the row's elements in
+// ascending order (incidence iptr/ient), per element its geometry (gradients of the
+// barycentric coordinates and volume), then
+//   B[q][(c, j)] += -|T| sum_a (grad lambda_a)_c R[a][m][n],  j = elem_dof[t][n],
+//   M[q][r']     +=  |T| Mr[m][r],                            r' = elem_p[t][r],
+// q being local pressure node m of element t. Within one element every (n, c) and every
+// r hits a different entry, so the lanes share an element and the elements follow one
+// another (ascending element order per entry, as on the host).
+__global__ void ks_assemble_blocks(int64_t np, int64_t nh, int nu, int npl, const double *__restrict__ xyz,
+                                   const int32_t *__restrict__ tets, const int32_t *__restrict__ elem_dof,
+                                   const int32_t *__restrict__ elem_p, const double *__restrict__ R,
+                                   const double *__restrict__ Mr, const int64_t *__restrict__ iptr,
+                                   const int64_t *__restrict__ ient, const int64_t *__restrict__ bptr,
+                                   const int32_t *__restrict__ bcol, double *__restrict__ bval,
+                                   const int64_t *__restrict__ mptr, const int32_t *__restrict__ mcol,
+                                   double *__restrict__ mval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= np) return;  // whole warp
+    const int64_t b0 = bptr[q], b1 = bptr[q + 1], m0 = mptr[q], m1 = mptr[q + 1];
+    for (int64_t x = iptr[q]; x < iptr[q + 1]; ++x) {
+        const int64_t t = ient[x] / 64;
+        const int m = (int)(ient[x] % 64);
+        double X[12];
+        for (int v = 0; v < 4; ++v)
+            for (int c = 0; c < 3; ++c) X[3 * v + c] = xyz[3 * (int64_t)tets[4 * t + v] + c];
+        double J[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) J[r][c] = X[3 * (c + 1) + r] - X[r];
+        const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        const double inv[3][3] = {{c00 / det, (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det,
+                                   (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det},
+                                  {c01 / det, (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det,
+                                   (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det},
+                                  {c02 / det, (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det,
+                                   (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det}};
+        double g[4][3];
+        for (int c = 0; c < 3; ++c) {
+            g[1][c] = inv[0][c];
+            g[2][c] = inv[1][c];
+            g[3][c] = inv[2][c];
+            g[0][c] = -(inv[0][c] + inv[1][c] + inv[2][c]);
+        }
+        const double vol = det / 6.0;
+        for (int idx = lane; idx < 3 * nu; idx += 32) {
+            const int n = idx / 3, c = idx % 3;
+            const int32_t j = elem_dof[t * nu + n];
+            if (j < 0) continue;
+            double sum = 0.0;
+            for (int a = 0; a < 4; ++a) sum += g[a][c] * R[((int64_t)a * npl + m) * nu + n];
+            const int32_t col = (int32_t)(c * nh + j);
+            const int64_t pos = ks_lower_bound(bcol, b0, b1, col);
+            if (pos < b1 && bcol[pos] == col) bval[pos] += -vol * sum;
+        }
+        for (int r = lane; r < npl; r += 32) {
+            const int32_t col = elem_p[t * npl + r];
+            const int64_t pos = ks_lower_bound(mcol, m0, m1, col);
+            if (pos < m1 && mcol[pos] == col) mval[pos] += vol * Mr[(int64_t)m * npl + r];
+        }
+        __syncwarp();
+    }
+}
+
+// one thread per item (no grid-stride loop): blocks to cover n threads
+unsigned ks_cover(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + kBlock - 1) / kBlock); }
+
+// B^T values: entry o copies B entry src[o]; diagonal of M_p
+__global__ void ks_gather_vals(int64_t n, const int64_t *__restrict__ src, const double *__restrict__ from,
+                               double *__restrict__ to) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < n) to[o] = from[src[o]];
+}
+
+__global__ void ks_diag(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                        const double *__restrict__ val, double *__restrict__ d) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = 0.0;
+    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e)
+        if (col[e] == (int32_t)i) v = val[e];
+    d[i] = v;
+}
 
 // y_c = A_h x_c for one velocity component
 template <int TPR>
@@ -328,24 +425,57 @@ void stokes_setup(pkasp_problem *p, int mp_iters, cudaStream_t s) {
     if (!p->have_setup) fail(PKASP_ESTATE, "pkasp_setup (the velocity preconditioner) must come first");
     if (mp_iters < 1 || mp_iters > 1000) fail(PKASP_EINVAL, "mp_iters must be 1..1000");
     stokes_free(p);
-    HCSR B, BT, M;
-    int64_t np = 0;
-    stokes_assemble(p, B, BT, M, np);
+    // patterns and reference tensors on the host (like the A_h pattern), values on the device
+    StokesPattern P;
+    stokes_patterns(p->k, p->nv, p->nt, p->xyz.data(), p->tets.data(), p->nh, p->elem_dof.data(), P);
+    const int64_t np = P.np;
     p->st = new StokesWork();
     StokesWork &S = *p->st;
     S.nh = p->nh;
     S.np = np;
     S.n = 3 * p->nh + np;
     S.mp_iters = mp_iters;
-    dcsr_upload(S.pool, S.B, B, s);
-    dcsr_upload(S.pool, S.BT, BT, s);
-    dcsr_upload(S.pool, S.M, M, s);
-    std::vector<double> d(np, 0.0);
-    for (int64_t i = 0; i < np; ++i)
-        for (int64_t e = M.ptr[i]; e < M.ptr[i + 1]; ++e)
-            if (M.col[e] == i) d[i] = M.val[e];
-    S.mdiag = S.pool.get<double>(std::max<int64_t>(np, 1));
-    PK_CUDA(cudaMemcpyAsync(S.mdiag, d.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+    dcsr_upload(S.pool, S.B, P.B, s);  // values zeroed (pattern only)
+    dcsr_upload(S.pool, S.BT, P.BT, s);
+    dcsr_upload(S.pool, S.M, P.M, s);
+    {
+        DevPool tmp;
+        try {
+            auto up = [&](const auto &v) {
+                using T = typename std::decay<decltype(v[0])>::type;
+                T *d = tmp.get<T>(std::max<size_t>(v.size(), 1));
+                if (!v.empty()) PK_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+                return d;
+            };
+            const int32_t *d_elem_p = up(P.elem_p);
+            const double *d_R = up(P.R);
+            const double *d_Mr = up(P.Mr);
+            const int64_t *d_iptr = up(P.iptr);
+            const int64_t *d_ient = up(P.ient);
+            const int64_t *d_src = up(P.bt_src);
+            if (np > 0) {
+                ks_assemble_blocks<<<ks_cover(np * 32), kBlock, 0, s>>>(
+                    np, p->nh, P.nu, P.npl, p->d_xyz, p->d_tets, p->d_elem_dof, d_elem_p, d_R, d_Mr, d_iptr, d_ient,
+                    S.B.ptr, S.B.col, S.B.val, S.M.ptr, S.M.col, S.M.val);
+                PK_LAUNCH();
+            }
+            if (S.BT.nnz > 0) {
+                ks_gather_vals<<<ks_cover(S.BT.nnz), kBlock, 0, s>>>(S.BT.nnz, d_src, S.B.val, S.BT.val);
+                PK_LAUNCH();
+            }
+            S.mdiag = S.pool.get<double>(std::max<int64_t>(np, 1));
+            if (np > 0) {
+                ks_diag<<<ks_cover(np), kBlock, 0, s>>>(np, S.M.ptr, S.M.col, S.M.val, S.mdiag);
+                PK_LAUNCH();
+            }
+            PK_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            tmp.free_all();
+            throw;
+        }
+        tmp.free_all();
+    }
     const int64_t nu = std::max<int64_t>(3 * p->nh, 1), npp = std::max<int64_t>(np, 1);
     S.t = S.pool.get<double>(nu);
     S.rr = S.pool.get<double>(npp);
