@@ -86,7 +86,7 @@ ORACLE_SAMPLE_ITERS = 12
 # one S_k application), keyed by (workload, cubes per side, smoother layout); a kernel
 # changed since the capture has no entry (traffic null)
 SMOOTHER_TRAFFIC = {("p4_n48_lognormal", 48, "CSR x4 lanes"): 11.308e9}
-SPMV_TRAFFIC = {("p4_n48_lognormal", 48): (6843780864 + 81747712 + 6830649600 + 90946816 + 6830844928 + 90865664) / 3}
+SPMV_TRAFFIC = {}
 NOMINAL_HBM_GBS = 8000.0  # GB300's nominal HBM3e bandwidth, for the second fraction
 # AMG level smoother: l1-Jacobi (1), one kernel per smoothing step; multicolour GS on the
 # dense coarse levels needs one launch per colour and costs ~25x more per V-cycle here
@@ -385,6 +385,9 @@ def main():
     ap.add_argument("--only-fp64", action="store_true",
                     help="time the FP64 solve only (profiler runs): no e2e, FP32, l1-Jacobi or "
                          "FGMRES legs")
+    ap.add_argument("--only-fp32", action="store_true",
+                    help="time the FP32-preconditioner solve only (profiler runs), with "
+                         "--smoother-layout-fp32")
     args = ap.parse_args()
     if args.mesh_n and args.workload not in SINGLE and args.workload != BATCHED["name"]:
         ap.error("--mesh-n applies to the p3, p4 and multi-RHS workloads")
@@ -431,7 +434,11 @@ def main():
     assemble_s = time.perf_counter() - t_as
     graph = 0 if args.eager else 1
     t_su = time.perf_counter()
-    G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, use_graph=graph, smoother_layout=args.smoother_layout)
+    if args.only_fp32:
+        G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, use_graph=graph, precond_precision=1,
+                smoother_layout=args.smoother_layout_fp32)
+    else:
+        G.setup(theta=0.25, level_smoother=LEVEL_SMOOTHER, use_graph=graph, smoother_layout=args.smoother_layout)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_su
     b = G.rhs()
@@ -445,11 +452,12 @@ def main():
     sol_s = ms / 1e3 / args.steps
     true_rel64 = st["true_rel"][0]
     info64 = G.info
-    if args.only_fp64:
+    if args.only_fp64 or args.only_fp32:
         if rank == 0:
+            flag = "--only-fp32" if args.only_fp32 else "--only-fp64"
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                               "warmup": args.warmup, "ms_per_step": ms / args.steps, "config": CONFIG,
-                              "note": "--only-fp64 profiler run: not a bench line"}))
+                              "note": f"{flag} profiler run: not a bench line"}))
         return
 
     # end to end through the C ABI with pinned host buffers: H2D of b, D2H of x (the solve
@@ -518,11 +526,11 @@ def main():
                           "frac": s_tf / FP64_PEAK_TFLOPS, "flops_per_application": smoother_flops,
                           "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM"}}
     achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
-    roof_spmv = {"bound": "hbm", "kernel": "k_spmv_pq / k_sell_spmv (fine SpMV, SELL-32, FP64)",
+    roof_spmv = {"bound": "hbm", "kernel": "k_spmv_q / k_sell_spmv (fine SpMV, SELL-32, FP64)",
                  "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                  "frac_of_nominal_8000": achieved / NOMINAL_HBM_GBS,
                  "traffic": SPMV_TRAFFIC.get((WORKLOAD["name"], WORKLOAD["n"])),
-                 "traffic_note": "ncu dram__bytes_read+write per launch (mean of 3), profiles/k_spmv_pq_p4_n48.md",
+                 "traffic_note": "ncu dram__bytes_read+write per launch (mean of 3), profiles/k_spmv_q_p4_n48.md",
                  "peak_source": src, "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms}
 
     def leg(**kw):

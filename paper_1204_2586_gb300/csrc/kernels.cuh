@@ -70,14 +70,41 @@ __device__ __forceinline__ A row_dot(int64_t lo, int64_t hi, int sub, const int3
 }
 
 // ---------------------------------------------------------------------------------
-// Deterministic grid reduction: every block writes its partial sums, the last block
-// to arrive adds the partials in block order and returns true (in all its threads).
+// Deterministic reductions. The order of every addition is fixed by the grid alone,
+// never by timing.
+//  - strided_sum: thread t of a block adds a[lo + t], a[lo + t + blockDim], ... below
+//    hi in that order (loads issued eight at a time).
+//  - block_partials: a warp shuffle tree, then the block's warps in order, into
+//    partials[block].
+//  - grid_reduce: the last block to arrive (fence and atomic counter) adds the block
+//    partials with strided_sum and a block tree.
+// The reductions run in element-wise kernels of kRedGrid blocks. GB300 issues one
+// warp-wide FP64 instruction per 16 cycles per SM, so a shuffle tree of doubles at the
+// end of every warp of a one-row-per-thread SpMV (5 adds per 32 rows) costs about as
+// much as streaming the operand vectors once more: the fine SpMV writes q only, and the
+// dot products read their vectors in a kernel of their own.
 // ---------------------------------------------------------------------------------
+__device__ __forceinline__ double strided_sum(const double *a, int64_t lo, int64_t hi, int stride_nv, int q) {
+    constexpr int U = 8;
+    const int64_t bd = blockDim.x;
+    double x = 0.0;
+    for (int64_t b0 = lo + threadIdx.x; b0 < hi; b0 += U * bd) {
+        double t[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t b = b0 + u * bd;
+            t[u] = b < hi ? __ldcg(&a[b * stride_nv + q]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (b0 + u * bd < hi) x += t[u];
+    }
+    return x;
+}
+
 template <int NV>
-__device__ __forceinline__ bool grid_reduce(double (&v)[NV], double *partials, unsigned *counter,
-                                            double (&tot)[NV]) {
+__device__ __forceinline__ void block_partials(double (&v)[NV], double *partials) {
     __shared__ double sh[NV][32];
-    __shared__ int last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
@@ -94,6 +121,16 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double *partials, u
             for (int w = 0; w < nw; ++w) s += sh[q][w];
             partials[(int64_t)blockIdx.x * NV + q] = s;
         }
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], double *partials, unsigned *counter,
+                                            double (&tot)[NV]) {
+    __shared__ double sh[NV][32];
+    __shared__ int last;
+    block_partials<NV>(v, partials);
+    if (threadIdx.x == 0) {
         __threadfence();
         unsigned prev = atomicAdd(counter, 1u);
         last = (prev == gridDim.x - 1);
@@ -101,10 +138,10 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double *partials, u
     __syncthreads();
     if (!last) return false;
     __threadfence();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-        double x = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) x += __ldcg(&partials[(int64_t)b * NV + q]);
+        double x = strided_sum(partials, 0, gridDim.x, NV, q);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
         if (lane == 0) sh[q][wid] = x;

@@ -425,9 +425,10 @@ void restrict_vcycle(pkasp_problem *p, const double *r, cudaStream_t s) {
     vcycle<PT>(p, 0, s, pd);
 }
 
-// z = B r
+// z = B r. tail = false (additive mode only) stops before the last step z = z_s + Pi w:
+// the PCG iteration then runs that step inside k_prolong_beta.
 template <typename PT>
-void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s) {
+void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s, bool tail = true) {
     PT *zs = pickw<PT>(p->w_zs, p->w_zs32);
     Level &L0 = p->lev[0];
     if (p->opt.mode == PKASP_MODE_AMG) {
@@ -446,6 +447,7 @@ void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s) 
         smoother<PT>(p, r, zs, s);
         PK_CUDA(cudaEventRecord(p->ev_join, p->aux_stream));
         PK_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+        if (!tail) return;
         k_prolong_add<PT, double><<<elem_grid(p->nh), kBlock, 0, s>>>(
             p->nh, p->Pi.ptr, p->Pi.col, pick<PT>(p->Pi.val, p->Pi.val32), lv_x<PT>(L0), zs, z);
         PK_LAUNCH();
@@ -521,30 +523,56 @@ __global__ void k_state_restart(PcgState *st) {
     st->loops = 0;
 }
 
-// r = b - A x, ||r||; on the first start also r0 and hist[0]
+// The fine-operator kernels (one thread or lane group per row, tens of thousands of
+// blocks) only write vectors; every dot product and norm is taken by an element-wise
+// kernel of kRedGrid blocks (grid_reduce). Each thread of those loads kVec elements
+// (i, i + stride, ...) before it computes, and adds its terms in ascending i as a
+// one-at-a-time loop would.
+constexpr int kVec = 4;
+
+// r = b - A x
 template <int TPR>
-__global__ void __launch_bounds__(kBlock) k_init_residual(int64_t n, RowOp A, const double *__restrict__ b,
-                                                          const double *__restrict__ x, double *__restrict__ r,
-                                                          PcgState *st, double *partials, unsigned *counter,
-                                                          double *hist) {
+__global__ void __launch_bounds__(kBlock) k_residual_fine(int64_t n, RowOp A, const double *__restrict__ b,
+                                                          const double *__restrict__ x, double *__restrict__ r) {
+    for_rows<TPR>(n, A, x, [&](int64_t row, double s) { r[row] = b[row] - s; });
+}
+
+// ||v||^2 of the grid, in every thread of the last block (grid_reduce)
+__device__ __forceinline__ bool grid_norm2(int64_t n, const double *__restrict__ v, double *partials,
+                                           unsigned *counter, double &tot) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double part = 0.0;
-    for_rows<TPR>(n, A, x, [&](int64_t row, double s) {
-        double ri = b[row] - s;
-        r[row] = ri;
-        part += ri * ri;
-    });
-    double v[1] = {part}, tot[1];
-    if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-        double rn = sqrt(tot[0]);
-        st->rnorm[0] = rn;
-        if (st->iter[0] == 0) {
-            st->r0[0] = rn;
-            if (st->hist_cap > 0) hist[0] = rn;
-            if (rn == 0.0) {
-                st->done[0] = 1;
-                st->status[0] = PKASP_OK;
-                st->all_done = 1;
-            }
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVec * stride) {
+        double t[kVec] = {};
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) t[u] = v[i];
+        }
+#pragma unroll
+        for (int u = 0; u < kVec; ++u)
+            if (i0 + u * stride < n) part += t[u] * t[u];
+    }
+    double a[1] = {part}, s[1];
+    const bool last = grid_reduce<1>(a, partials, counter, s);
+    tot = s[0];
+    return last;
+}
+
+// ||r||; on the first start also r0 and hist[0]
+__global__ void __launch_bounds__(kBlock) k_init_norm(int64_t n, const double *__restrict__ r, PcgState *st,
+                                                      double *partials, unsigned *counter, double *hist) {
+    double tot;
+    if (!grid_norm2(n, r, partials, counter, tot) || threadIdx.x != 0) return;
+    double rn = sqrt(tot);
+    st->rnorm[0] = rn;
+    if (st->iter[0] == 0) {
+        st->r0[0] = rn;
+        if (st->hist_cap > 0) hist[0] = rn;
+        if (rn == 0.0) {
+            st->done[0] = 1;
+            st->status[0] = PKASP_OK;
+            st->all_done = 1;
         }
     }
 }
@@ -554,27 +582,60 @@ __global__ void __launch_bounds__(kBlock) k_start(int64_t n, const double *__res
                                                   const double *__restrict__ z, double *__restrict__ p,
                                                   PcgState *st, double *partials, unsigned *counter) {
     if (st->done[0]) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double part = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double zi = z[i];
-        p[i] = zi;
-        part += r[i] * zi;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVec * stride) {
+        double rv[kVec] = {}, zv[kVec] = {};
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                rv[u] = r[i];
+                zv[u] = z[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                p[i] = zv[u];
+                part += rv[u] * zv[u];
+            }
+        }
     }
     double v[1] = {part}, tot[1];
     if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) st->rho[0] = tot[0];
 }
 
-// q = A p, alpha = rho / (p, q)
+// q = A p
 template <int TPR>
-__global__ void __launch_bounds__(kBlock) k_spmv_pq(int64_t n, RowOp A, const double *__restrict__ p,
-                                                    double *__restrict__ q, PcgState *st, double *partials,
-                                                    unsigned *counter) {
+__global__ void __launch_bounds__(kBlock) k_spmv_q(int64_t n, RowOp A, const double *__restrict__ p,
+                                                   double *__restrict__ q, const PcgState *st) {
     if (st->done[0]) return;
+    for_rows<TPR>(n, A, p, [&](int64_t row, double s) { q[row] = s; });
+}
+
+// alpha = rho / (p, q)
+__global__ void __launch_bounds__(kBlock) k_pq_alpha(int64_t n, const double *__restrict__ p,
+                                                     const double *__restrict__ q, PcgState *st, double *partials,
+                                                     unsigned *counter) {
+    if (st->done[0]) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double part = 0.0;
-    for_rows<TPR>(n, A, p, [&](int64_t row, double s) {
-        q[row] = s;
-        part += p[row] * s;
-    });
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVec * stride) {
+        double pv[kVec] = {}, qv[kVec] = {};
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                pv[u] = p[i];
+                qv[u] = q[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVec; ++u)
+            if (i0 + u * stride < n) part += pv[u] * qv[u];
+    }
     double v[1] = {part}, tot[1];
     if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) {
         double pq = tot[0];
@@ -595,12 +656,30 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(int64_t n, double *__restr
                                                       double *hist) {
     if (st->done[0]) return;
     const double a = st->alpha[0];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double part = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] += a * p[i];
-        double ri = r[i] - a * q[i];
-        r[i] = ri;
-        part += ri * ri;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVec * stride) {
+        double xv[kVec] = {}, rv[kVec] = {}, pv[kVec] = {}, qv[kVec] = {};
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                xv[u] = x[i];
+                rv[u] = r[i];
+                pv[u] = p[i];
+                qv[u] = q[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                x[i] = xv[u] + a * pv[u];
+                double ri = rv[u] - a * qv[u];
+                r[i] = ri;
+                part += ri * ri;
+            }
+        }
     }
     double v[1] = {part}, tot[1];
     if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) {
@@ -626,11 +705,90 @@ __global__ void __launch_bounds__(kBlock) k_beta(int64_t n, const double *__rest
                                                  const double *__restrict__ z, const double *__restrict__ q,
                                                  int flexible, PcgState *st, double *partials, unsigned *counter) {
     if (st->done[0]) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double a0 = 0.0, a1 = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double zi = z[i];
-        a0 += r[i] * zi;
-        a1 += zi * q[i];
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVec * stride) {
+        double rv[kVec] = {}, zv[kVec] = {}, qv[kVec] = {};
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                rv[u] = r[i];
+                zv[u] = z[i];
+                qv[u] = q[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            if (i0 + u * stride < n) {
+                a0 += rv[u] * zv[u];
+                a1 += zv[u] * qv[u];
+            }
+        }
+    }
+    double v[2] = {a0, a1}, tot[2];
+    if (grid_reduce<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        double rho = st->rho[0];
+        st->beta[0] = flexible ? (-st->alpha[0] * tot[1]) / rho : tot[0] / rho;
+        st->rho[0] = tot[0];
+    }
+}
+
+// The additive preconditioner's last step fused with the beta kernel: z = z_s + Pi w
+// (row sums in PT in ascending entry order, as k_prolong_add), then (r, z) and (z, q)
+// and beta as k_beta. The same arithmetic in the same order as the two kernels, without
+// the round trip of z through memory.
+template <typename PT>
+__global__ void __launch_bounds__(kBlock) k_prolong_beta(int64_t n, const int64_t *__restrict__ ptr,
+                                                         const int32_t *__restrict__ col, const PT *__restrict__ val,
+                                                         const PT *__restrict__ w, const PT *__restrict__ zs,
+                                                         const double *__restrict__ r, const double *__restrict__ q,
+                                                         double *__restrict__ z, int flexible, PcgState *st,
+                                                         double *partials, unsigned *counter) {
+    if (st->done[0]) return;
+    constexpr int V = 2;  // rows in flight per thread (more would spill)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double a0 = 0.0, a1 = 0.0;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += V * stride) {
+        int64_t lo[V], hi[V];
+        PT sv[V];
+        double zv[V] = {}, rv[V] = {}, qv[V] = {};
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int64_t i = i0 + u * stride;
+            const bool ok = i < n;
+            lo[u] = ok ? ptr[i] : 0;
+            hi[u] = ok ? ptr[i + 1] : 0;
+            sv[u] = PT(0);
+            if (ok) {
+                zv[u] = (double)zs[i];
+                rv[u] = r[i];
+                qv[u] = q[i];
+            }
+        }
+        // I_P rows hold at most 4 entries (one per vertex of the element); the loop
+        // below takes any longer row too
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+                const int64_t e = lo[u] + t;
+                if (e < hi[u]) sv[u] += val[e] * w[col[e]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u)
+            for (int64_t e = lo[u] + 4; e < hi[u]; ++e) sv[u] += val[e] * w[col[e]];
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                const double zi = zv[u] + (double)sv[u];
+                z[i] = zi;
+                a0 += rv[u] * zi;
+                a1 += zi * qv[u];
+            }
+        }
     }
     double v[2] = {a0, a1}, tot[2];
     if (grid_reduce<2>(v, partials, counter, tot) && threadIdx.x == 0) {
@@ -645,8 +803,23 @@ __global__ void __launch_bounds__(kBlock) k_update_p(int64_t n, const double *__
                                                      const PcgState *st) {
     if (st->done[0]) return;
     const double b = st->beta[0];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = z[i] + b * p[i];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVec * stride) {
+        double zv[kVec] = {}, pv[kVec] = {};
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                zv[u] = z[i];
+                pv[u] = p[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) p[i] = zv[u] + b * pv[u];
+        }
+    }
 }
 
 // loop control of the captured while node: continue unless stopped; a safety bound on
@@ -658,18 +831,11 @@ __global__ void k_loop_control(PcgState *st, cudaGraphConditionalHandle h) {
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
-// true residual norm ||b - A x|| into st->tnorm
-template <int TPR>
-__global__ void __launch_bounds__(kBlock) k_true_residual(int64_t n, RowOp A, const double *__restrict__ b,
-                                                          const double *__restrict__ x, PcgState *st,
-                                                          double *partials, unsigned *counter) {
-    double part = 0.0;
-    for_rows<TPR>(n, A, x, [&](int64_t row, double s) {
-        double ri = b[row] - s;
-        part += ri * ri;
-    });
-    double v[1] = {part}, tot[1];
-    if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) st->tnorm[0] = sqrt(tot[0]);
+// true residual norm ||t|| (t = b - A x) into st->tnorm
+__global__ void __launch_bounds__(kBlock) k_true_norm(int64_t n, const double *__restrict__ t, PcgState *st,
+                                                      double *partials, unsigned *counter) {
+    double tot;
+    if (grid_norm2(n, t, partials, counter, tot) && threadIdx.x == 0) st->tnorm[0] = sqrt(tot);
 }
 
 }  // namespace
@@ -946,8 +1112,10 @@ namespace {
 void enqueue_init(pkasp_problem *p, const double *b, double *x, cudaStream_t s) {
     const int tpr = p->spmv_tpr;
     const RowOp A = fine_op(p);
-    PK_FMT_SWITCH(tpr, (k_init_residual<TPR><<<fine_grid(p), kBlock, 0, s>>>(
-                           p->nh, A, b, x, p->w_r, p->d_state, p->d_partials, p->d_counter, p->d_hist)));
+    const unsigned fg = fine_grid(p);
+    PK_FMT_SWITCH(tpr, (k_residual_fine<TPR><<<fg, kBlock, 0, s>>>(p->nh, A, b, x, p->w_r)));
+    PK_LAUNCH();
+    k_init_norm<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_r, p->d_state, p->d_partials, p->d_counter, p->d_hist);
     PK_LAUNCH();
     apply_prec(p, p->w_r, p->w_z, s);
     k_start<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_r, p->w_z, p->w_p, p->d_state, p->d_partials,
@@ -960,16 +1128,32 @@ void enqueue_iteration(pkasp_problem *p, double *x, cudaStream_t s) {
     const int tpr = p->spmv_tpr;
     const RowOp A = fine_op(p);
     const unsigned fg = fine_grid(p);
-    PK_FMT_SWITCH(tpr, (k_spmv_pq<TPR><<<fg, kBlock, 0, s>>>(p->nh, A, p->w_p, p->w_q, p->d_state,
-                                                             p->d_partials, p->d_counter)));
+    PK_FMT_SWITCH(tpr, (k_spmv_q<TPR><<<fg, kBlock, 0, s>>>(p->nh, A, p->w_p, p->w_q, p->d_state)));
+    PK_LAUNCH();
+    k_pq_alpha<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_p, p->w_q, p->d_state, p->d_partials, p->d_counter);
     PK_LAUNCH();
     k_update_xr<<<kRedGrid, kBlock, 0, s>>>(p->nh, x, p->w_r, p->w_p, p->w_q, p->d_state, p->d_partials,
                                                   p->d_counter, p->d_hist);
     PK_LAUNCH();
-    apply_prec(p, p->w_r, p->w_z, s);
     const int flex = (p->opt.flexible || p->opt.precond_precision == PKASP_PREC_FP32) ? 1 : 0;
-    k_beta<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_r, p->w_z, p->w_q, flex, p->d_state, p->d_partials,
-                                             p->d_counter);
+    if (p->opt.mode == PKASP_MODE_ADDITIVE) {
+        // additive preconditioner up to z_s and w; z = z_s + Pi w inside the beta kernel
+        if (p->opt.precond_precision == PKASP_PREC_FP32) {
+            precondition<float>(p, p->w_r, p->w_z, s, false);
+            k_prolong_beta<float><<<kRedGrid, kBlock, 0, s>>>(
+                p->nh, p->Pi.ptr, p->Pi.col, p->Pi.val32, p->lev[0].x32, p->w_zs32, p->w_r, p->w_q, p->w_z, flex,
+                p->d_state, p->d_partials, p->d_counter);
+        } else {
+            precondition<double>(p, p->w_r, p->w_z, s, false);
+            k_prolong_beta<double><<<kRedGrid, kBlock, 0, s>>>(
+                p->nh, p->Pi.ptr, p->Pi.col, p->Pi.val, p->lev[0].x, p->w_zs, p->w_r, p->w_q, p->w_z, flex,
+                p->d_state, p->d_partials, p->d_counter);
+        }
+    } else {
+        apply_prec(p, p->w_r, p->w_z, s);
+        k_beta<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_r, p->w_z, p->w_q, flex, p->d_state, p->d_partials,
+                                                 p->d_counter);
+    }
     PK_LAUNCH();
     k_update_p<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_z, p->w_p, p->d_state);
     PK_LAUNCH();
@@ -978,8 +1162,11 @@ void enqueue_iteration(pkasp_problem *p, double *x, cudaStream_t s) {
 void enqueue_final(pkasp_problem *p, const double *b, const double *x, cudaStream_t s) {
     const int tpr = p->spmv_tpr;
     const RowOp A = fine_op(p);
-    PK_FMT_SWITCH(tpr, (k_true_residual<TPR><<<fine_grid(p), kBlock, 0, s>>>(p->nh, A, b, x, p->d_state,
-                                                                             p->d_partials, p->d_counter)));
+    const unsigned fg = fine_grid(p);
+    // the residual goes to a work vector the iteration no longer needs
+    PK_FMT_SWITCH(tpr, (k_residual_fine<TPR><<<fg, kBlock, 0, s>>>(p->nh, A, b, x, p->w_t)));
+    PK_LAUNCH();
+    k_true_norm<<<kRedGrid, kBlock, 0, s>>>(p->nh, p->w_t, p->d_state, p->d_partials, p->d_counter);
     PK_LAUNCH();
 }
 
