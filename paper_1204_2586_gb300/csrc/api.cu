@@ -159,6 +159,7 @@ int pkasp_assemble(const double *xyz_host, int64_t nv, const int32_t *tets_host,
         pk::dcsr_upload(pool, p->AH, D.AH_pattern, s);
         pk::dcsr_upload(pool, p->Pi, D.Pi, s);
         pk::dcsr_upload(pool, p->PiT, D.PiT, s);
+        pk::pi_codes_upload(pool, D.Pi, D.PiT, k, p->pic, s);
         p->d_b = pool.get<double>(p->nh);
         p->d_flag = pool.get<int>(4);
         PK_CUDA(cudaStreamSynchronize(s));

@@ -49,6 +49,20 @@ struct DCSR {
     float *val32 = nullptr;  // FP32 copy for the mixed-precision preconditioner
 };
 
+// I_P with its values as codes. Every entry of I_P is a nodal value m / k (m = 1..k) of
+// a P1 basis function at a Lagrange node (Eq. 10), so an entry needs its column and one
+// byte: the PCG iteration's prolongation reads a 4-wide row layout (no row pointers) and
+// the restriction I_P^T r reads one-byte codes instead of values. Built at assembly when
+// every entry has that form (it always has for the meshes this library builds).
+struct PiCodes {
+    bool ok = false;
+    int32_t *ell_col = nullptr;    // [n_h][4] columns of the rows of I_P, -1 past a row's end
+    uint32_t *ell_code = nullptr;  // [n_h] byte q = code m of entry q of the row (0 past its end)
+    uint8_t *t_code = nullptr;     // [nnz] codes of I_P^T, in its CSR order
+    double *tab = nullptr;         // [8] tab[m] = m / k (tab[0] = 0)
+    float *tab32 = nullptr;        // [8] (float) tab[m]
+};
+
 // Host CSR (setup and tests).
 struct HCSR {
     int64_t n = 0, m = 0;
@@ -161,6 +175,7 @@ struct pkasp_problem {
     int32_t *d_inc = nullptr, *d_vinc = nullptr;  // packed tet*64 + local
     // operators
     pk::DCSR Ah, AH, Pi, PiT;
+    pk::PiCodes pic;  // I_P and I_P^T with coded values (iteration transfers)
     double *d_b = nullptr;
     double assemble_ms = 0, setup_ms = 0;
     // setup
@@ -329,6 +344,7 @@ void exclusive_scan(int64_t *d, int64_t n, cudaStream_t s);  // in place, d[n] =
 int64_t read_i64(const int64_t *d, cudaStream_t s);
 void dcsr_alloc(DevPool &pool, DCSR &a, int64_t n, int64_t m, int64_t nnz);
 void dcsr_upload(DevPool &pool, DCSR &a, const HCSR &h, cudaStream_t s);
+void pi_codes_upload(DevPool &pool, const HCSR &Pi, const HCSR &PiT, int k, PiCodes &pc, cudaStream_t s);
 void dcsr_download(const DCSR &a, HCSR &h, cudaStream_t s);
 void dcsr_make32(DevPool &pool, DCSR &a, cudaStream_t s);
 

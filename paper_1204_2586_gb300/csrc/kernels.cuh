@@ -195,6 +195,44 @@ __global__ void __launch_bounds__(kBlock) k_restrict_jacobi0(int64_t n, const in
     }
 }
 
+// b = I_P^T x with I_P^T's values given by one-byte codes (value tab[code]), fused like
+// k_restrict_jacobi0 with the level's first l1-Jacobi step xc = b / l1; the same lanes,
+// batches and order of additions as row_dot, so the result equals k_restrict_jacobi0's
+template <int TPR, typename PT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_restrict_code_jacobi0(int64_t n, const int64_t *__restrict__ ptr,
+                                                                  const int32_t *__restrict__ col,
+                                                                  const uint8_t *__restrict__ code,
+                                                                  const PT *__restrict__ tab,
+                                                                  const XT *__restrict__ x,
+                                                                  const PT *__restrict__ l1, PT *__restrict__ b,
+                                                                  PT *__restrict__ xc) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gt / TPR;
+    const int sub = threadIdx.x & (TPR - 1);
+    const bool ok = row < n;
+    const int64_t lo = ok ? ptr[row] : 0, hi = ok ? ptr[row + 1] : 0;
+    PT acc = PT(0);
+    for (int64_t base = lo + sub; base < hi; base += kBatch * TPR) {
+        int c[kBatch];
+        PT v[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int64_t e = base + (int64_t)k * TPR;
+            const bool in = e < hi;
+            c[k] = in ? ldg(&col[e]) : -1;
+            v[k] = in ? ldg(&tab[ldg(&code[e])]) : PT(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k)
+            if (c[k] >= 0) acc += v[k] * (PT)ldg(&x[c[k]]);
+    }
+    acc = subwarp_sum<TPR>(acc);
+    if (ok && sub == 0) {
+        b[row] = acc;
+        xc[row] = acc / l1[row];
+    }
+}
+
 // r = b - A x
 template <int TPR, typename A, typename VT, typename T>
 __global__ void __launch_bounds__(kBlock) k_residual(int64_t n, const int64_t *__restrict__ ptr,

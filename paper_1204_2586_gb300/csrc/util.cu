@@ -162,6 +162,55 @@ void dcsr_upload(DevPool &pool, DCSR &a, const HCSR &h, cudaStream_t s) {
     PK_CUDA(cudaStreamSynchronize(s));  // host vectors may go out of scope
 }
 
+void pi_codes_upload(DevPool &pool, const HCSR &Pi, const HCSR &PiT, int k, PiCodes &pc, cudaStream_t s) {
+    pc = PiCodes();
+    if (k < 1 || k > 7) return;
+    auto code_of = [k](double v) -> int {
+        for (int m = 1; m <= k; ++m)
+            if (v == (double)m / k) return m;
+        return -1;
+    };
+    const int64_t n = Pi.n;
+    std::vector<int32_t> ec((size_t)4 * n, -1);
+    std::vector<uint32_t> ecode((size_t)n, 0u);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t lo = Pi.ptr[i], hi = Pi.ptr[i + 1];
+        if (hi - lo > 4) return;
+        for (int64_t e = lo; e < hi; ++e) {
+            const int m = code_of(Pi.val[e]);
+            if (m < 0) return;
+            ec[(size_t)4 * i + (e - lo)] = Pi.col[e];
+            ecode[i] |= (uint32_t)m << (8 * (e - lo));
+        }
+    }
+    std::vector<uint8_t> tc(PiT.val.size());
+    for (size_t e = 0; e < tc.size(); ++e) {
+        const int m = code_of(PiT.val[e]);
+        if (m < 0) return;
+        tc[e] = (uint8_t)m;
+    }
+    double tab[8];
+    float tab32[8];
+    for (int m = 0; m < 8; ++m) {
+        tab[m] = (m >= 1 && m <= k) ? (double)m / k : 0.0;
+        tab32[m] = (float)tab[m];
+    }
+    pc.ell_col = pool.get<int32_t>((size_t)4 * std::max<int64_t>(n, 1));
+    pc.ell_code = pool.get<uint32_t>(std::max<int64_t>(n, 1));
+    pc.t_code = pool.get<uint8_t>(std::max<size_t>(tc.size(), 1));
+    pc.tab = pool.get<double>(8);
+    pc.tab32 = pool.get<float>(8);
+    if (n > 0) {
+        PK_CUDA(cudaMemcpyAsync(pc.ell_col, ec.data(), sizeof(int32_t) * ec.size(), cudaMemcpyHostToDevice, s));
+        PK_CUDA(cudaMemcpyAsync(pc.ell_code, ecode.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
+    }
+    if (!tc.empty()) PK_CUDA(cudaMemcpyAsync(pc.t_code, tc.data(), tc.size(), cudaMemcpyHostToDevice, s));
+    PK_CUDA(cudaMemcpyAsync(pc.tab, tab, sizeof(tab), cudaMemcpyHostToDevice, s));
+    PK_CUDA(cudaMemcpyAsync(pc.tab32, tab32, sizeof(tab32), cudaMemcpyHostToDevice, s));
+    PK_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+    pc.ok = true;
+}
+
 void dcsr_download(const DCSR &a, HCSR &h, cudaStream_t s) {
     h.n = a.n;
     h.m = a.m;
