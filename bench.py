@@ -11,13 +11,17 @@ The metric is MDOF*iter/s = n_h * iterations / solve time; the time to solution 
 HBM roofline of the dominant kernel are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload p4_n48_lognormal | p3_n32 | p2_n64_batched48 | ...]
+                    [--workload p4_n48_lognormal | p3_n32 | p2_n8 | p2_n64_batched48 |
+                                p3_n24_adjoint | ...]
 
-p3_n32 is the P3 problem on 32^3 cubes (857,375 unknowns, kappa = 1). p2_n64_batched48
-is the multi-RHS solve: the P2 vector Laplacian (3 velocity components, identical scalar
+p3_n32 is the P3 problem on 32^3 cubes (857,375 unknowns, kappa = 1), p2_n8 the P2
+problem on 8^3 cubes (3,375 unknowns; launch-latency bound). p2_n64_batched48 is the
+multi-RHS solve: the P2 vector Laplacian (3 velocity components, identical scalar
 blocks) on a 64^3 jittered Kuhn mesh with 16 right-hand sides of i.i.d. N(0,1) entries
 (seed 2), i.e. 48 columns of the scalar system in one blocked PCG, FP32 preconditioner
-and FP64 outer iteration.
+and FP64 outer iteration. p3_n24_adjoint is the differentiable solve: P3 on 24^3 cubes
+with lognormal kappa, one step = forward PCG + adjoint PCG + dL/dkappa for
+L = 0.5 ||u - u_obs||^2.
 
 Multi-GPU: the path runs as independent replicas (one solve per rank, no collective on
 the data path); value sums the ranks' work over the slowest rank's time.
@@ -62,7 +66,31 @@ CONFIG_P4 = {
     "l2_flush": "inputs larger than L2: A_h alone is 6.2 GB vs 129 MB L2",
     "parallelism": "replicas (one independent solve per GPU)",
 }
-SINGLE = {WORKLOAD["name"]: (WORKLOAD, CONFIG), P4["name"]: (P4, CONFIG_P4)}
+P2_8 = dict(name="p2_n8", k=2, n=8, jitter=0.2, mesh_seed=0)
+CONFIG_P2_8 = {
+    "workload": "P2 Poisson, kappa=1, 8^3 jittered Kuhn cubes (3,072 tets, 3,375 unknowns), sine source, "
+                "FP64, PCG to rel. residual 1e-8, additive aux-space preconditioner (1 SGS sweep + 1 P1 AMG "
+                "V-cycle, theta=0.25, l1-Jacobi level smoothing); launch-latency bound at this size",
+    "mesh": "unit cube, 8^3 cubes x 6 Kuhn tets, interior vertices jittered by <=0.2h (seed 0)",
+    "k": 2,
+    "n_h": 3375,
+    "l2_flush": "none: the whole problem (under 1 MB) stays in L2; a latency measurement",
+    "parallelism": "replicas (one independent solve per GPU)",
+}
+SINGLE = {WORKLOAD["name"]: (WORKLOAD, CONFIG), P4["name"]: (P4, CONFIG_P4), P2_8["name"]: (P2_8, CONFIG_P2_8)}
+ADJOINT = dict(name="p3_n24_adjoint", k=3, n=24, jitter=0.2, mesh_seed=0, kappa_seed=1, obs_kappa_seed=3)
+CONFIG_ADJOINT = {
+    "workload": "P3 Poisson on 24^3 jittered Kuhn cubes (82,944 tets, 357,911 unknowns), kappa_e = exp(N(0,1)) "
+                "(seed 1), sine source; loss L = 0.5 ||u - u_obs||^2 with u_obs solved for a second kappa "
+                "field (seed 3); one step = forward PCG + adjoint PCG (right-hand side u - u_obs) + dL/dkappa "
+                "for every element (dL/db = the adjoint solution); FP32 preconditioner, FP64 outer "
+                "flexible CG, rel. residual 1e-8; value counts forward and adjoint iterations",
+    "mesh": "unit cube, 24^3 cubes x 6 Kuhn tets, interior vertices jittered by <=0.2h (seed 0)",
+    "k": 3,
+    "n_h": 357911,
+    "l2_flush": "none: A_h (about 170 MB) is only a little larger than L2",
+    "parallelism": "replicas (one independent solve per GPU)",
+}
 DEFAULT_WORKLOAD = P4["name"]
 BATCHED = dict(name="p2_n64_batched48", k=2, n=64, jitter=0.2, mesh_seed=0, rhs_seed=2, ncols=48)
 CONFIG_BATCHED = {
@@ -297,7 +325,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": CONFIG_BATCHED if batched else SINGLE[args.workload][1],
+            "data": "synthetic", "config": CONFIG_BATCHED if batched else CONFIG,
             "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -368,8 +396,8 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=[WORKLOAD["name"], P4["name"], BATCHED["name"], "theta_study", "cop_study",
-                             "stokes_study"])
+                    choices=[WORKLOAD["name"], P4["name"], P2_8["name"], BATCHED["name"], ADJOINT["name"],
+                             "theta_study", "cop_study", "stokes_study"])
     ap.add_argument("--smoother-layout", type=int, default=0,
                     help="pin the fine smoother layout (pkasp_options.smoother_layout) instead of "
                          "autotuning it; for profiler runs, under which the autotuner's timings "
@@ -393,6 +421,8 @@ def main():
         ap.error("--mesh-n applies to the p3, p4 and multi-RHS workloads")
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == ADJOINT["name"]:
+        WORKLOAD, CONFIG = ADJOINT, CONFIG_ADJOINT
     if args.workload in SINGLE:
         WORKLOAD, CONFIG = SINGLE[args.workload]
         if args.mesh_n:  # a smaller case of the same workload (profiler captures)
@@ -422,6 +452,11 @@ def main():
         return
     if args.workload == "stokes_study":
         run_stokes_study(args)
+        return
+    if args.workload == ADJOINT["name"]:
+        run_adjoint(args, ws, rank, local)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
         return
     if args.workload == BATCHED["name"]:
         run_batched(args, ws, rank, local)
@@ -877,6 +912,127 @@ def run_batched(args, ws, rank, local):
                         "solve_ms_per_step": sum(e_dev) / len(e_dev)},
                 "gpu_launches": launches, "roofline": roof, "roofline_smoother": roof_sm,
                 "cpu_baseline": cpu}
+        line.update(extra)
+        print(json.dumps(line))
+
+
+def run_adjoint(args, ws, rank, local):
+    """One step = forward solve, adjoint solve and dL/dkappa (the backward pass of the
+    differentiable solve for L = 0.5 ||u - u_obs||^2), inputs resident on the device.
+    value = n_h * (forward + adjoint iterations) / time. e2e: the same through the public
+    differentiable API (autograd.solve + loss.backward()) with kappa uploaded from pinned
+    host memory and dL/dkappa read back every step; that path also re-assembles A_h for
+    kappa and rebuilds the preconditioner inside every forward call."""
+    import torch
+
+    from paper_1204_2586_gb300 import Problem
+    from paper_1204_2586_gb300 import autograd as pag
+    from paper_1204_2586_gb300.inputs import kappa_lognormal, kuhn_mesh
+
+    wl = ADJOINT
+    prec = dict(theta=0.25, level_smoother=LEVEL_SMOOTHER, precond_precision=1,
+                use_graph=0 if args.eager else 1)
+    t_as = time.perf_counter()
+    xyz, tets = kuhn_mesh(wl["n"], wl["jitter"], wl["mesh_seed"])
+    nt = tets.shape[0]
+    kap_obs = kappa_lognormal(nt, wl["obs_kappa_seed"])
+    kap = kappa_lognormal(nt, wl["kappa_seed"])
+    G = Problem(xyz, tets, wl["k"], kap_obs)
+    torch.cuda.synchronize()
+    assemble_s = time.perf_counter() - t_as
+    G.setup(**prec)
+    b = G.rhs()
+    u_obs, st_obs = G.solve(b)
+    assert st_obs["status"][0] == 0, st_obs
+    G.set_kappa(kap)
+    t_su = time.perf_counter()
+    G.setup(**prec)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_su
+    nh = G.nh
+    u = torch.zeros_like(b)
+    lam = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        u.zero_()
+        _, st = G.solve(b, u)
+        g = u - u_obs
+        lam.zero_()
+        _, sta = G.solve_adjoint(g, lam)
+        dk = G.grad_kappa(u, lam)
+        assert st["status"][0] == 0 and sta["status"][0] == 0, (st, sta)
+        return st["iters"][0] + sta["iters"][0], st, sta, dk
+
+    launches = 0
+
+    for _ in range(args.warmup):
+        step()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = []
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed_solves")
+        e0.record(stream)
+        for _ in range(args.steps):
+            n_it, st, sta, dk = step()
+            its.append(n_it)
+            launches += st["kernel_launches"] + sta["kernel_launches"] + 1  # + k_grad_kappa
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms, work = replica_totals(e0.elapsed_time(e1), nh * sum(its))
+    value = work / (ms / 1e3) / 1e6
+
+    # end to end through torch.autograd: kappa from pinned host memory, dL/dkappa back
+    kh = torch.tensor(kap, dtype=torch.float64).pin_memory()
+    gh = torch.empty(nt, dtype=torch.float64).pin_memory()
+    e_its = []
+
+    def e2e_step():
+        kd = kh.to("cuda", non_blocking=True).requires_grad_(True)
+        uu = pag.solve(kd, b, G, **prec)
+        loss = 0.5 * torch.sum((uu - u_obs) ** 2)
+        loss.backward()
+        gh.copy_(kd.grad)
+        return uu
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+        e_its.append(its[-1])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_ms, e2e_work = replica_totals(e2e_s * 1e3, nh * sum(e_its))
+    e2e_value = e2e_work / (e2e_ms / 1e3) / 1e6
+    extra = {"time_per_step_s": ms / 1e3 / args.steps, "forward_iterations": st["iters"][0],
+             "adjoint_iterations": sta["iters"][0], "forward_true_rel_residual": st["true_rel"][0],
+             "adjoint_true_rel_residual": sta["true_rel"][0], "setup_s": setup_s, "assemble_s": assemble_s,
+             "grad_kappa_norm": float(torch.linalg.norm(dk))}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            _, cpu = run_cpu_oracle(1, 0)
+            cpu.pop("seconds", None)
+        except Exception as e:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": CONFIG_ADJOINT, "clocks": clk.summary(),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * nt,
+                        "d2h_bytes_per_step": 8 * nt, "ms_per_step": e2e_ms / args.steps,
+                        "includes": "re-assembly of A_h for kappa and the preconditioner setup in every "
+                                    "forward call of the differentiable solve"},
+                "gpu_launches": launches, "cpu_baseline": cpu}
         line.update(extra)
         print(json.dumps(line))
 

@@ -198,7 +198,7 @@ class Problem:
         L.check(L.load().pkasp_solve_adjoint(self.h, _ptr(g), _ptr(lam), ncols, ld, C.byref(st),
                                              _stream(stream)))
         return lam, dict(iters=list(st.iters[:ncols]), status=list(st.status[:ncols]),
-                         true_rel=list(st.true_rel[:ncols]))
+                         true_rel=list(st.true_rel[:ncols]), kernel_launches=int(st.kernel_launches))
 
     # ---- Stokes (Taylor-Hood P_k - P_{k-1}) ---------------------------------------
     def stokes_setup(self, mp_iters=10, stream=None):
