@@ -78,11 +78,13 @@ __device__ __forceinline__ A row_dot(int64_t lo, int64_t hi, int sub, const int3
 //    partials[block].
 //  - grid_reduce: the last block to arrive (fence and atomic counter) adds the block
 //    partials with strided_sum and a block tree.
-// The reductions run in element-wise kernels of kRedGrid blocks. GB300 issues one
+// The PCG's reductions run in element-wise kernels of kRedGrid blocks. GB300 issues one
 // warp-wide FP64 instruction per 16 cycles per SM, so a shuffle tree of doubles at the
 // end of every warp of a one-row-per-thread SpMV (5 adds per 32 rows) costs about as
-// much as streaming the operand vectors once more: the fine SpMV writes q only, and the
-// dot products read their vectors in a kernel of their own.
+// much as streaming the operand vectors once more: the PCG's fine SpMV writes q only,
+// and the dot products read their vectors in a kernel of their own. FGMRES's residual
+// and the Stokes operator (off the headline path) still reduce inside their full-grid
+// kernels.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ double strided_sum(const double *a, int64_t lo, int64_t hi, int stride_nv, int q) {
     constexpr int U = 8;

@@ -21,10 +21,11 @@ inline RowOp fine_op(const pkasp_problem *p) {
     return RowOp{p->Ah.ptr, p->Ah.col, p->Ah.val, nullptr};
 }
 
-// Grid of the fused kernels that read A_h through for_rows and reduce at most one value:
-// a thread (SELL-32) or sub-warp (CSR) per row, as in the plain SpMV, up to the capacity
-// of the partials buffer (kRedGrid * 4 * PKASP_MAX_COLS values). A grid of kRedGrid
-// blocks striding over the rows left the fused SpMV at about 1.5x the plain one's time.
+// Grid of the kernels that read A_h through for_rows (some of them reduce one value
+// with grid_reduce): a thread (SELL-32) or sub-warp (CSR) per row, as in the plain
+// SpMV, up to the capacity of the partials buffer (kRedGrid * 4 * PKASP_MAX_COLS
+// values). A grid of kRedGrid blocks striding over the rows left the SpMV at about 1.5x
+// the plain one's time.
 inline unsigned fine_grid(const pkasp_problem *p) {
     const int64_t threads = p->nh * (p->spmv_tpr > 0 ? p->spmv_tpr : 1);
     const int64_t g = std::max<int64_t>(1, (threads + kBlock - 1) / kBlock);
