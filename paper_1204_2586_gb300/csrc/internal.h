@@ -52,10 +52,8 @@ struct DCSR {
 // I_P with its values as codes. Every entry of I_P is a nodal value m / k (m = 1..k) of
 // a P1 basis function at a Lagrange node (Eq. 10), so an entry needs its column and one
 // byte: the PCG iteration's prolongation reads a 4-wide row layout (no row pointers) and
-// the restriction I_P^T r reads one-byte codes instead of values. Built at assembly when
-// every entry has that form (it always has for the meshes this library builds).
+// the restriction I_P^T r reads one-byte codes instead of values. Built at assembly.
 struct PiCodes {
-    bool ok = false;
     int32_t *ell_col = nullptr;    // [n_h][4] columns of the rows of I_P, -1 past a row's end
     uint32_t *ell_code = nullptr;  // [n_h] byte q = code m of entry q of the row (0 past its end)
     uint8_t *t_code = nullptr;     // [nnz] codes of I_P^T, in its CSR order

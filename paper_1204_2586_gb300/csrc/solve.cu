@@ -280,7 +280,7 @@ bool restrict_to(pkasp_problem *p, const DCSR &R, const XT *x, int l, cudaStream
         spmv<PT, PT>(R, x, lv_b<PT>(L), tpr_of(R), s);
         return false;
     }
-    if (&R == &p->PiT && p->pic.ok) {
+    if (&R == &p->PiT) {
         // I_P^T with one-byte value codes
         PK_TPR_SWITCH(tpr_of(R), (k_restrict_code_jacobi0<TPR, PT, XT><<<rows_grid(R.n, TPR), kBlock, 0, s>>>(
                                      R.n, R.ptr, R.col, p->pic.t_code, pick<PT>(p->pic.tab, p->pic.tab32), x,
@@ -743,74 +743,13 @@ __global__ void __launch_bounds__(kBlock) k_beta(int64_t n, const double *__rest
 }
 
 // The additive preconditioner's last step fused with the beta kernel: z = z_s + Pi w
-// (row sums in PT in ascending entry order, as k_prolong_add), then (r, z) and (z, q)
-// and beta as k_beta. The same arithmetic in the same order as the two kernels, without
-// the round trip of z through memory.
+// (row sums in PT in entry order, then one FP64 add, as k_prolong_add computes them),
+// then (r, z) and (z, q) and beta as k_beta, without the round trip of z through memory
+// between two kernels. I_P is read in its coded 4-wide layout: one 16-byte load of a
+// row's columns and one word of value codes instead of row pointers, columns and
+// values.
 template <typename PT>
-__global__ void __launch_bounds__(kBlock) k_prolong_beta(int64_t n, const int64_t *__restrict__ ptr,
-                                                         const int32_t *__restrict__ col, const PT *__restrict__ val,
-                                                         const PT *__restrict__ w, const PT *__restrict__ zs,
-                                                         const double *__restrict__ r, const double *__restrict__ q,
-                                                         double *__restrict__ z, int flexible, PcgState *st,
-                                                         double *partials, unsigned *counter) {
-    if (st->done[0]) return;
-    constexpr int V = 2;  // rows in flight per thread (more would spill)
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    double a0 = 0.0, a1 = 0.0;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += V * stride) {
-        int64_t lo[V], hi[V];
-        PT sv[V];
-        double zv[V] = {}, rv[V] = {}, qv[V] = {};
-#pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const int64_t i = i0 + u * stride;
-            const bool ok = i < n;
-            lo[u] = ok ? ptr[i] : 0;
-            hi[u] = ok ? ptr[i + 1] : 0;
-            sv[u] = PT(0);
-            if (ok) {
-                zv[u] = (double)zs[i];
-                rv[u] = r[i];
-                qv[u] = q[i];
-            }
-        }
-        // I_P rows hold at most 4 entries (one per vertex of the element); the loop
-        // below takes any longer row too
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-#pragma unroll
-            for (int u = 0; u < V; ++u) {
-                const int64_t e = lo[u] + t;
-                if (e < hi[u]) sv[u] += val[e] * w[col[e]];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < V; ++u)
-            for (int64_t e = lo[u] + 4; e < hi[u]; ++e) sv[u] += val[e] * w[col[e]];
-#pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const int64_t i = i0 + u * stride;
-            if (i < n) {
-                const double zi = zv[u] + (double)sv[u];
-                z[i] = zi;
-                a0 += rv[u] * zi;
-                a1 += zi * qv[u];
-            }
-        }
-    }
-    double v[2] = {a0, a1}, tot[2];
-    if (grid_reduce<2>(v, partials, counter, tot) && threadIdx.x == 0) {
-        double rho = st->rho[0];
-        st->beta[0] = flexible ? (-st->alpha[0] * tot[1]) / rho : tot[0] / rho;
-        st->rho[0] = tot[0];
-    }
-}
-
-// k_prolong_beta with I_P in its coded 4-wide layout: one 16-byte load of a row's
-// columns and one word of codes instead of row pointers, columns and values; the same
-// arithmetic in the same order
-template <typename PT>
-__global__ void __launch_bounds__(kBlock) k_prolong_beta_ell(int64_t n, const int4 *__restrict__ ecol,
+__global__ void __launch_bounds__(kBlock) k_prolong_beta(int64_t n, const int4 *__restrict__ ecol,
                                                              const uint32_t *__restrict__ ecode,
                                                              const PT *__restrict__ tab, const PT *__restrict__ w,
                                                              const PT *__restrict__ zs, const double *__restrict__ r,
@@ -1206,24 +1145,14 @@ void enqueue_iteration(pkasp_problem *p, double *x, cudaStream_t s) {
         const PiCodes &pc = p->pic;
         if (p->opt.precond_precision == PKASP_PREC_FP32) {
             precondition<float>(p, p->w_r, p->w_z, s, false);
-            if (pc.ok)
-                k_prolong_beta_ell<float><<<kRedGrid, kBlock, 0, s>>>(
-                    p->nh, (const int4 *)pc.ell_col, pc.ell_code, pc.tab32, p->lev[0].x32, p->w_zs32, p->w_r,
-                    p->w_q, p->w_z, flex, p->d_state, p->d_partials, p->d_counter);
-            else
-                k_prolong_beta<float><<<kRedGrid, kBlock, 0, s>>>(
-                    p->nh, p->Pi.ptr, p->Pi.col, p->Pi.val32, p->lev[0].x32, p->w_zs32, p->w_r, p->w_q, p->w_z,
-                    flex, p->d_state, p->d_partials, p->d_counter);
+            k_prolong_beta<float><<<kRedGrid, kBlock, 0, s>>>(
+                p->nh, (const int4 *)pc.ell_col, pc.ell_code, pc.tab32, p->lev[0].x32, p->w_zs32, p->w_r, p->w_q,
+                p->w_z, flex, p->d_state, p->d_partials, p->d_counter);
         } else {
             precondition<double>(p, p->w_r, p->w_z, s, false);
-            if (pc.ok)
-                k_prolong_beta_ell<double><<<kRedGrid, kBlock, 0, s>>>(
-                    p->nh, (const int4 *)pc.ell_col, pc.ell_code, pc.tab, p->lev[0].x, p->w_zs, p->w_r, p->w_q,
-                    p->w_z, flex, p->d_state, p->d_partials, p->d_counter);
-            else
-                k_prolong_beta<double><<<kRedGrid, kBlock, 0, s>>>(
-                    p->nh, p->Pi.ptr, p->Pi.col, p->Pi.val, p->lev[0].x, p->w_zs, p->w_r, p->w_q, p->w_z, flex,
-                    p->d_state, p->d_partials, p->d_counter);
+            k_prolong_beta<double><<<kRedGrid, kBlock, 0, s>>>(
+                p->nh, (const int4 *)pc.ell_col, pc.ell_code, pc.tab, p->lev[0].x, p->w_zs, p->w_r, p->w_q,
+                p->w_z, flex, p->d_state, p->d_partials, p->d_counter);
         }
     } else {
         apply_prec(p, p->w_r, p->w_z, s);

@@ -164,7 +164,9 @@ void dcsr_upload(DevPool &pool, DCSR &a, const HCSR &h, cudaStream_t s) {
 
 void pi_codes_upload(DevPool &pool, const HCSR &Pi, const HCSR &PiT, int k, PiCodes &pc, cudaStream_t s) {
     pc = PiCodes();
-    if (k < 1 || k > 7) return;
+    // every entry of I_P is m / k by construction (mesh.cpp); anything else is a bug
+    auto bad = [](const char *what) { fail(PKASP_EMESH, std::string("I_P: ") + what); };
+    if (k < 1 || k > 7) bad("degree outside 1..7");
     auto code_of = [k](double v) -> int {
         for (int m = 1; m <= k; ++m)
             if (v == (double)m / k) return m;
@@ -175,10 +177,10 @@ void pi_codes_upload(DevPool &pool, const HCSR &Pi, const HCSR &PiT, int k, PiCo
     std::vector<uint32_t> ecode((size_t)n, 0u);
     for (int64_t i = 0; i < n; ++i) {
         const int64_t lo = Pi.ptr[i], hi = Pi.ptr[i + 1];
-        if (hi - lo > 4) return;
+        if (hi - lo > 4) bad("a row with more than 4 entries");
         for (int64_t e = lo; e < hi; ++e) {
             const int m = code_of(Pi.val[e]);
-            if (m < 0) return;
+            if (m < 0) bad("an entry that is not m / k");
             ec[(size_t)4 * i + (e - lo)] = Pi.col[e];
             ecode[i] |= (uint32_t)m << (8 * (e - lo));
         }
@@ -186,7 +188,7 @@ void pi_codes_upload(DevPool &pool, const HCSR &Pi, const HCSR &PiT, int k, PiCo
     std::vector<uint8_t> tc(PiT.val.size());
     for (size_t e = 0; e < tc.size(); ++e) {
         const int m = code_of(PiT.val[e]);
-        if (m < 0) return;
+        if (m < 0) bad("an entry of the transpose that is not m / k");
         tc[e] = (uint8_t)m;
     }
     double tab[8];
@@ -208,7 +210,6 @@ void pi_codes_upload(DevPool &pool, const HCSR &Pi, const HCSR &PiT, int k, PiCo
     PK_CUDA(cudaMemcpyAsync(pc.tab, tab, sizeof(tab), cudaMemcpyHostToDevice, s));
     PK_CUDA(cudaMemcpyAsync(pc.tab32, tab32, sizeof(tab32), cudaMemcpyHostToDevice, s));
     PK_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
-    pc.ok = true;
 }
 
 void dcsr_download(const DCSR &a, HCSR &h, cudaStream_t s) {
