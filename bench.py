@@ -601,6 +601,7 @@ def main():
                             "true_rel_residual": stg["true_rel"][0], "restarts": stg["restarts"]}
     extra = {"time_to_solution_s": sol_s, "iterations": iters[-1], "true_rel_residual": true_rel64,
              "setup_s": setup_s, "assemble_s": assemble_s, "levels": int(info64.levels),
+             "l2_persist_bytes": int(info64.l2_persist_bytes),
              "level_rows": [int(v) for v in info64.level_rows[: info64.levels]],
              "fine_colours": int(info64.fine_colours), "op_complexity": info64.op_complexity,
              "spmv_layout": "SELL-32" if info64.spmv_layout == 0 else f"CSR x{info64.spmv_layout} lanes",

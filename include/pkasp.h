@@ -107,7 +107,16 @@ typedef struct {
                              name: a strong F neighbour k of i adds its strong C points to
                              i's interpolatory set only when k shares no strong C point
                              with i; 0: extended+i [0] */
-    int reserved[1];
+    int l2_persist;       /* 1: with the FP64 preconditioner and the SGS smoother, keep the
+                             fine smoother's vector (8 n_h bytes) in the L2 persisting
+                             set-aside during its colour phases: an access-policy window
+                             (persisting hits, streaming misses) on every phase launch.
+                             Applied when that vector is at least a quarter of L2 and
+                             1.125x it fits the largest set-aside; setup then raises the
+                             context's cudaLimitPersistingL2CacheSize to 1.125x the vector
+                             if it is lower, and pkasp_destroy resets the persisting lines
+                             and restores the limit it found. A cache hint only: results
+                             are bitwise the same. 0: never [1] */
 } pkasp_options;
 
 /* Problem sizes after assembly and (for the AMG entries) after setup. */
@@ -138,6 +147,9 @@ typedef struct {
     int block_group;        /* columns per group of the multi-RHS fine smoother phases,
                                autotuned at the first solve of a width (0 before) */
     int block_lanes;        /* threads per row of those phases (autotuned with it) */
+    int64_t l2_persist_bytes; /* bytes of the fine smoother's vector kept in the L2
+                               persisting set-aside after setup (options.l2_persist);
+                               0: none */
 } pkasp_info;
 
 /* Per-solve statistics, filled by pkasp_solve (which synchronises the stream). */

@@ -31,7 +31,7 @@ class pkasp_options(C.Structure):
                 ("flexible", C.c_int), ("precond_precision", C.c_int), ("use_graph", C.c_int),
                 ("spmv_threads", C.c_int), ("smoother_layout", C.c_int), ("krylov", C.c_int),
                 ("restart", C.c_int), ("interp_pmax", C.c_int), ("interp_trunc", C.c_int),
-                ("interp_cc", C.c_int), ("reserved", C.c_int * 1)]
+                ("interp_cc", C.c_int), ("l2_persist", C.c_int)]
 
 
 class pkasp_info(C.Structure):
@@ -43,7 +43,8 @@ class pkasp_info(C.Structure):
                 ("level_colours", C.c_int * MAX_LEVELS), ("op_complexity", C.c_double),
                 ("setup_ms", C.c_double), ("assemble_ms", C.c_double),
                 ("spmv_layout", C.c_int), ("smoother_layout", C.c_int),
-                ("block_width", C.c_int), ("block_group", C.c_int), ("block_lanes", C.c_int)]
+                ("block_width", C.c_int), ("block_group", C.c_int), ("block_lanes", C.c_int),
+                ("l2_persist_bytes", C.c_int64)]
 
 
 class pkasp_stats(C.Structure):

@@ -78,6 +78,7 @@ void pkasp_default_options(pkasp_options *o) {
     o->interp_pmax = 0;
     o->interp_trunc = 0;
     o->interp_cc = 0;
+    o->l2_persist = 1;
 }
 
 int pkasp_last_error(char *buf, size_t n) {
@@ -210,6 +211,7 @@ int pkasp_problem_info(const pkasp_problem *p, pkasp_info *info) {
         info->block_width = p->bwork_nc > 0 ? p->bwork_nc : 0;
         info->block_group = p->bgroup_cols;
         info->block_lanes = p->blanes;
+        info->l2_persist_bytes = (int64_t)p->l2_win_bytes;
     }
     return PKASP_OK;
 }
@@ -261,6 +263,7 @@ int pkasp_setup(pkasp_problem *p, const pkasp_options *opt, pkasp_stream_t strea
     if (o.interp_pmax < 0 || o.interp_trunc < 0 || o.interp_trunc > 999)
         return set_error(PKASP_EINVAL, "interp_pmax must be >= 0 and interp_trunc 0..999");
     if (o.interp_cc != 0 && o.interp_cc != 1) return set_error(PKASP_EINVAL, "interp_cc must be 0 or 1");
+    if (o.l2_persist != 0 && o.l2_persist != 1) return set_error(PKASP_EINVAL, "l2_persist must be 0 or 1");
     if (o.krylov != PKASP_KRYLOV_CG && o.krylov != PKASP_KRYLOV_FGMRES)
         return set_error(PKASP_EINVAL, "krylov must be PKASP_KRYLOV_CG or PKASP_KRYLOV_FGMRES");
     if (o.krylov == PKASP_KRYLOV_FGMRES && (o.restart < 1 || o.restart > 256))
@@ -370,6 +373,7 @@ int pkasp_destroy(pkasp_problem *p) {
     pk::stokes_free(p);
     p->stage_pool.free_all();
     p->pool.free_all();
+    pk::l2_window_release(p);
     if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);

@@ -174,6 +174,11 @@ struct pkasp_problem {
     // operators
     pk::DCSR Ah, AH, Pi, PiT;
     pk::PiCodes pic;  // I_P and I_P^T with coded values (iteration transfers)
+    // L2 persisting window of the fine smoother's vector (options.l2_persist)
+    size_t l2_win_bytes = 0;    // window size used by the colour phases (0: none)
+    bool l2_raised = false;     // this problem raised the context's persisting limit
+    size_t l2_prev_limit = 0;   // the limit found before raising it
+    size_t l2_set_limit = 0;    // the limit this problem set
     double *d_b = nullptr;
     double assemble_ms = 0, setup_ms = 0;
     // setup
@@ -343,6 +348,7 @@ int64_t read_i64(const int64_t *d, cudaStream_t s);
 void dcsr_alloc(DevPool &pool, DCSR &a, int64_t n, int64_t m, int64_t nnz);
 void dcsr_upload(DevPool &pool, DCSR &a, const HCSR &h, cudaStream_t s);
 void pi_codes_upload(DevPool &pool, const HCSR &Pi, const HCSR &PiT, int k, PiCodes &pc, cudaStream_t s);
+void l2_window_release(pkasp_problem *p);
 void dcsr_download(const DCSR &a, HCSR &h, cudaStream_t s);
 void dcsr_make32(DevPool &pool, DCSR &a, cudaStream_t s);
 

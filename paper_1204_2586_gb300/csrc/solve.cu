@@ -7,6 +7,7 @@
 // and run concurrently on two streams (two branches of the captured graph). One PCG
 // iteration is a fixed kernel sequence; the whole solve is captured once into a CUDA
 // graph whose while-node repeats the iteration until a device-side flag says stop.
+#include <type_traits>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -91,20 +92,32 @@ void spmv(const DCSR &A, const X *x, Y *y, int tpr, cudaStream_t s) {
 // Launch with programmatic stream serialization (PDL): the kernel may begin while the
 // previous kernel on the stream drains; it must call pdl_wait() before reading anything
 // an earlier kernel wrote (k_gs_phase does).
+// win (optional): an L2 access-policy window for the launch
 template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+void launch_pdl_w(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, const cudaAccessPolicyWindow *win,
+                  Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kBlock);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (win) {
+        attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[1].val.accessPolicyWindow = *win;
+        cfg.numAttrs = 2;
+    }
     PK_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
     PK_LAUNCH();
+}
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+    launch_pdl_w(kern, grid, s, (const cudaAccessPolicyWindow *)nullptr, args...);
 }
 
 // Lanes per row for a colour phase whose longest row part has `len` entries: the fewest
@@ -164,16 +177,17 @@ unsigned phase_grid(int64_t rows, int tpr) {
 // colour phases of a forward sweep from zero: y = (D+L)^{-1} r; tpr < 0 picks the lanes
 // per colour from the colour's longest lower part
 template <typename PT, typename TR>
-void gs_forward0(const DSplit &sp, int tpr_fixed, const TR *r, PT *y, cudaStream_t s) {
+void gs_forward0(const DSplit &sp, int tpr_fixed, const TR *r, PT *y, cudaStream_t s,
+                 const cudaAccessPolicyWindow *win = nullptr) {
     for (int c = 0; c < sp.ncol; ++c) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
         if (tpr_fixed > 400) {  // grid-stride with prefetch of the next row
             const int tpr = tpr_fixed % 100;
             const int nb = batch_for(tpr, sp.l90[c]);
-            PK_TPR3_SWITCH(tpr, PK_NB3_SWITCH(nb, (launch_pdl(
+            PK_TPR3_SWITCH(tpr, PK_NB3_SWITCH(nb, (launch_pdl_w(
                 k_gs_phase_gs<TPR, NB, PT, TR, false>,
-                phase_grid<k_gs_phase_gs<TPR, NB, PT, TR, false>>(pe - pb, TPR), s, pb, pe,
+                phase_grid<k_gs_phase_gs<TPR, NB, PT, TR, false>>(pe - pb, TPR), s, win, pb, pe,
                 (const int32_t *)sp.perm, (const int64_t *)sp.lptr, (const int32_t *)sp.lcol,
                 pick<PT>(sp.lval, sp.lval32), pick<PT>(sp.dinv, sp.dinv32), r, y))));
             continue;
@@ -183,15 +197,15 @@ void gs_forward0(const DSplit &sp, int tpr_fixed, const TR *r, PT *y, cudaStream
         const int tpr = tf > 0 ? tf : lanes_for(sp.lmax[c]);
         const int nb = batch_for(tpr, sp.l90[c]);
         if (two) {
-            PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl(k_gs_phase2<TPR, NB, PT, TR, false>,
-                                                            rows_grid((pe - pb + 1) / 2, TPR), s, pb, pe,
+            PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl_w(k_gs_phase2<TPR, NB, PT, TR, false>,
+                                                            rows_grid((pe - pb + 1) / 2, TPR), s, win, pb, pe,
                                                             (const int32_t *)sp.perm, (const int64_t *)sp.lptr,
                                                             (const int32_t *)sp.lcol, pick<PT>(sp.lval, sp.lval32),
                                                             pick<PT>(sp.dinv, sp.dinv32), r, y))));
             continue;
         }
-        PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl(k_gs_phase<TPR, NB, PT, TR, false>,
-                                                        rows_grid(pe - pb, TPR), s, pb, pe,
+        PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl_w(k_gs_phase<TPR, NB, PT, TR, false>,
+                                                        rows_grid(pe - pb, TPR), s, win, pb, pe,
                                                         (const int32_t *)sp.perm, (const int64_t *)sp.lptr,
                                                         (const int32_t *)sp.lcol, pick<PT>(sp.lval, sp.lval32),
                                                         pick<PT>(sp.dinv, sp.dinv32), r, y))));
@@ -200,7 +214,8 @@ void gs_forward0(const DSplit &sp, int tpr_fixed, const TR *r, PT *y, cudaStream
 
 // backward half of the symmetric sweep from zero: y <- y - D^{-1} U y, colours C-1..0
 template <typename PT>
-void gs_backward0(const DSplit &sp, int tpr_fixed, PT *y, cudaStream_t s) {
+void gs_backward0(const DSplit &sp, int tpr_fixed, PT *y, cudaStream_t s,
+                  const cudaAccessPolicyWindow *win = nullptr) {
     // the highest colour has no upper part: its phase would leave y unchanged
     for (int c = sp.ncol - 2; c >= 0; --c) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
@@ -208,9 +223,9 @@ void gs_backward0(const DSplit &sp, int tpr_fixed, PT *y, cudaStream_t s) {
         if (tpr_fixed > 400) {
             const int tpr = tpr_fixed % 100;
             const int nb = batch_for(tpr, sp.u90[c]);
-            PK_TPR3_SWITCH(tpr, PK_NB3_SWITCH(nb, (launch_pdl(
+            PK_TPR3_SWITCH(tpr, PK_NB3_SWITCH(nb, (launch_pdl_w(
                 k_gs_phase_gs<TPR, NB, PT, PT, true>,
-                phase_grid<k_gs_phase_gs<TPR, NB, PT, PT, true>>(pe - pb, TPR), s, pb, pe,
+                phase_grid<k_gs_phase_gs<TPR, NB, PT, PT, true>>(pe - pb, TPR), s, win, pb, pe,
                 (const int32_t *)sp.perm, (const int64_t *)sp.uptr, (const int32_t *)sp.ucol,
                 pick<PT>(sp.uval, sp.uval32), pick<PT>(sp.dinv, sp.dinv32), (const PT *)y, y))));
             continue;
@@ -220,15 +235,15 @@ void gs_backward0(const DSplit &sp, int tpr_fixed, PT *y, cudaStream_t s) {
         const int tpr = tf > 0 ? tf : lanes_for(sp.umax[c]);
         const int nb = batch_for(tpr, sp.u90[c]);
         if (two) {
-            PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl(k_gs_phase2<TPR, NB, PT, PT, true>,
-                                                            rows_grid((pe - pb + 1) / 2, TPR), s, pb, pe,
+            PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl_w(k_gs_phase2<TPR, NB, PT, PT, true>,
+                                                            rows_grid((pe - pb + 1) / 2, TPR), s, win, pb, pe,
                                                             (const int32_t *)sp.perm, (const int64_t *)sp.uptr,
                                                             (const int32_t *)sp.ucol, pick<PT>(sp.uval, sp.uval32),
                                                             pick<PT>(sp.dinv, sp.dinv32), (const PT *)y, y))));
             continue;
         }
-        PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl(k_gs_phase<TPR, NB, PT, PT, true>,
-                                                        rows_grid(pe - pb, TPR), s, pb, pe,
+        PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_pdl_w(k_gs_phase<TPR, NB, PT, PT, true>,
+                                                        rows_grid(pe - pb, TPR), s, win, pb, pe,
                                                         (const int32_t *)sp.perm, (const int64_t *)sp.uptr,
                                                         (const int32_t *)sp.ucol, pick<PT>(sp.uval, sp.uval32),
                                                         pick<PT>(sp.dinv, sp.dinv32), (const PT *)y, y))));
@@ -423,8 +438,18 @@ void smoother(pkasp_problem *p, const double *r, PT *zs, cudaStream_t s) {
         }
         return;
     }
-    gs_forward0<PT, double>(p->fine, ts, r, zs, s);
-    gs_backward0<PT>(p->fine, ts, zs, s);
+    // FP64: the access-policy window that keeps zs in the L2 set-aside (l2_window_setup)
+    cudaAccessPolicyWindow win = {};
+    const bool use_win = std::is_same<PT, double>::value && p->l2_win_bytes > 0;
+    if (use_win) {
+        win.base_ptr = (void *)zs;
+        win.num_bytes = p->l2_win_bytes;
+        win.hitRatio = 1.0f;
+        win.hitProp = cudaAccessPropertyPersisting;
+        win.missProp = cudaAccessPropertyStreaming;
+    }
+    gs_forward0<PT, double>(p->fine, ts, r, zs, s, use_win ? &win : nullptr);
+    gs_backward0<PT>(p->fine, ts, zs, s, use_win ? &win : nullptr);
 }
 
 template <typename PT>
@@ -845,6 +870,52 @@ __global__ void __launch_bounds__(kBlock) k_true_norm(int64_t n, const double *_
 }  // namespace
 
 
+// L2 persisting window for the FP64 fine smoother (pkasp_options.l2_persist). The colour
+// phases gather the smoother's vector y (8 n_h bytes) once per entry, phase after phase,
+// while the matrix streams past it; when y is a sizeable part of L2 the stream evicts it
+// and every phase re-reads it from DRAM. Marking y's lines persisting keeps them. Only
+// when y is at least a quarter of L2 (smaller vectors stay resident anyway) and the
+// set-aside it needs (1.125 x y, measured best against 0.86 x and 1.5 x y) fits the
+// device's largest one. The limit is a property of the CUDA context, not of the GPU:
+// setup raises it if it is lower, pkasp_destroy restores what it found.
+void l2_window_setup(pkasp_problem *p) {
+    p->l2_win_bytes = 0;
+    const pkasp_options &o = p->opt;
+    if (!o.l2_persist || o.precond_precision != PKASP_PREC_FP64 || o.smoother != PKASP_SMOOTHER_SGS ||
+        o.mode != PKASP_MODE_ADDITIVE)
+        return;
+    int dev = 0, l2 = 0, maxp = 0;
+    PK_CUDA(cudaGetDevice(&dev));
+    PK_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    PK_CUDA(cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev));
+    const size_t y = sizeof(double) * (size_t)p->nh;
+    const size_t mb = size_t(1) << 20;
+    const size_t want = (y + y / 8 + mb - 1) / mb * mb;
+    if (maxp <= 0 || y < (size_t)l2 / 4 || want > (size_t)maxp) return;
+    size_t cur = 0;
+    PK_CUDA(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+    if (cur < want) {
+        if (!p->l2_raised) p->l2_prev_limit = cur;
+        PK_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+        PK_CUDA(cudaDeviceGetLimit(&p->l2_set_limit, cudaLimitPersistingL2CacheSize));
+        p->l2_raised = true;
+    }
+    p->l2_win_bytes = y;
+}
+
+// returns persisting lines to normal and restores the limit this problem raised (if no
+// one changed it since); never throws
+void l2_window_release(pkasp_problem *p) {
+    if (!p->l2_raised) return;
+    cudaCtxResetPersistingL2Cache();
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess && cur == p->l2_set_limit)
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, p->l2_prev_limit);
+    cudaGetLastError();
+    p->l2_raised = false;
+    p->l2_win_bytes = 0;
+}
+
 // ---------------------------------------------------------------------------------
 // setup orchestration
 // ---------------------------------------------------------------------------------
@@ -951,6 +1022,7 @@ void setup_device(pkasp_problem *p, cudaStream_t s) {
     free_setup(p);
     const pkasp_options &o = p->opt;
     const bool want32 = o.precond_precision == PKASP_PREC_FP32;
+    l2_window_setup(p);
     DevPool &pool = p->setup_pool;
     // fine level: colour split of A_h, l1 norms, FP32 copies
     build_split(pool, p->Ah, stream_colour(o.seed, 0), want32, p->fine, s);

@@ -101,6 +101,30 @@ def test_p4_solutions_solve_the_oracle_system(p4):
     assert np.linalg.norm(xs[1] - xs[0]) <= 1e-8 * np.linalg.norm(xs[0])
 
 
+@pytest.mark.slow
+def test_p4_l2_window_is_only_a_cache_hint(p4):
+    """At P4 48^3 the FP64 smoother's vector (56 MB) is kept in the L2 persisting
+    set-aside during the colour phases (options.l2_persist, the default); the FP32
+    preconditioner and l2_persist = 0 take no window. The window changes no result: with
+    the smoother layout pinned (the autotuner times the candidates, and the window can
+    change its pick), the solution and the residual history are bitwise those of the
+    solve without it."""
+    torch = _torch()
+    G, _ = p4
+    b = G.rhs()
+    out = {}
+    for flag in (1, 0):
+        G.setup(level_smoother=1, l2_persist=flag, smoother_layout=4)
+        assert G.info.l2_persist_bytes == (8 * G.nh if flag else 0)
+        x, st = G.solve(b, torch.zeros_like(b), hist_cap=128)
+        print(f"l2_persist={flag}: {st['iters'][0]} iterations, SpMV layout {G.info.spmv_layout}, "
+              f"smoother layout {G.info.smoother_layout}")
+        out[flag] = (x.cpu().numpy(), st["hist"])
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    G.setup(level_smoother=1, precond_precision=1)
+    assert G.info.l2_persist_bytes == 0
+
+
 @pytest.fixture(scope="module")
 def b48(oracle_mod):
     _torch()
