@@ -113,7 +113,7 @@ ORACLE_SAMPLE_ITERS = 12
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (summed over the phases of
 # one S_k application), keyed by (workload, cubes per side, smoother layout); a kernel
 # changed since the capture has no entry (traffic null)
-SMOOTHER_TRAFFIC = {("p4_n48_lognormal", 48, "CSR x4 lanes"): 11.308e9}
+SMOOTHER_TRAFFIC = {}
 SPMV_TRAFFIC = {("p4_n48_lognormal", 48): (6843905536 + 82143744 + 6831242496 + 91436544 + 6832146176 + 91604224) / 3}
 NOMINAL_HBM_GBS = 8000.0  # GB300's nominal HBM3e bandwidth, for the second fraction
 # AMG level smoother: l1-Jacobi (1), one kernel per smoothing step; multicolour GS on the

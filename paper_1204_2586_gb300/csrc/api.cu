@@ -323,6 +323,7 @@ static int solve_common(pkasp_problem *p, const double *b, double *x, int ncols,
             zero_cols(xx);
         }
         int rc = pk::solve_device(p, bb, xx, ncols, ld, st, s);
+        pk::l2_window_idle(p);  // the solve has synchronised its stream
         if (!xd) {
             if (from_zero && ld != ncols)
                 PK_CUDA(cudaMemcpy2DAsync(x, sizeof(double) * ld, xx, sizeof(double) * ld, sizeof(double) * ncols,
@@ -488,6 +489,7 @@ int pkasp_stokes_solve(pkasp_problem *p, const double *b_dev, double *x_dev, pka
     if (!p->st) return set_error(PKASP_ESTATE, "pkasp_stokes_setup first");
     return guarded([&]() -> int {
         const int rc = pk::stokes_solve(p, b_dev, x_dev, st, (cudaStream_t)stream);
+        pk::l2_window_idle(p);
         if (rc != PKASP_OK) return set_error(rc, "FGMRES on the Stokes system reached max_iter before the tolerance");
         return PKASP_OK;
     });
@@ -647,6 +649,7 @@ int pkasp_time_kernel(pkasp_problem *p, int which, int reps, float *ms_out, pkas
     if (!p->have_setup) return set_error(PKASP_ESTATE, "setup first");
     return guarded([&]() -> int {
         *ms_out = pk::time_kernel(p, which, reps, (cudaStream_t)stream);
+        pk::l2_window_idle(p);
         return PKASP_OK;
     });
 }

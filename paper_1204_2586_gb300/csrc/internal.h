@@ -349,6 +349,7 @@ void dcsr_alloc(DevPool &pool, DCSR &a, int64_t n, int64_t m, int64_t nnz);
 void dcsr_upload(DevPool &pool, DCSR &a, const HCSR &h, cudaStream_t s);
 void pi_codes_upload(DevPool &pool, const HCSR &Pi, const HCSR &PiT, int k, PiCodes &pc, cudaStream_t s);
 void l2_window_release(pkasp_problem *p);
+void l2_window_idle(pkasp_problem *p);
 void dcsr_download(const DCSR &a, HCSR &h, cudaStream_t s);
 void dcsr_make32(DevPool &pool, DCSR &a, cudaStream_t s);
 

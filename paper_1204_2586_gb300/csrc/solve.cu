@@ -870,6 +870,8 @@ __global__ void __launch_bounds__(kBlock) k_true_norm(int64_t n, const double *_
 }  // namespace
 
 
+void l2_window_release(pkasp_problem *p);
+
 // L2 persisting window for the FP64 fine smoother (pkasp_options.l2_persist). The colour
 // phases gather the smoother's vector y (8 n_h bytes) once per entry, phase after phase,
 // while the matrix streams past it; when y is a sizeable part of L2 the stream evicts it
@@ -882,8 +884,10 @@ void l2_window_setup(pkasp_problem *p) {
     p->l2_win_bytes = 0;
     const pkasp_options &o = p->opt;
     if (!o.l2_persist || o.precond_precision != PKASP_PREC_FP64 || o.smoother != PKASP_SMOOTHER_SGS ||
-        o.mode != PKASP_MODE_ADDITIVE)
+        o.mode != PKASP_MODE_ADDITIVE) {
+        l2_window_release(p);  // give back a set-aside an earlier setup of this problem took
         return;
+    }
     int dev = 0, l2 = 0, maxp = 0;
     PK_CUDA(cudaGetDevice(&dev));
     PK_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
@@ -901,6 +905,15 @@ void l2_window_setup(pkasp_problem *p) {
         p->l2_raised = true;
     }
     p->l2_win_bytes = y;
+}
+
+// after a synchronised solve: the smoother vector's lines go back to normal, so that the
+// set-aside serves ordinary accesses of whatever runs next (other solves, other problems,
+// the caller's kernels); the next S_k marks them persisting again. Never throws.
+void l2_window_idle(pkasp_problem *p) {
+    if (p->l2_win_bytes == 0) return;
+    cudaCtxResetPersistingL2Cache();
+    cudaGetLastError();
 }
 
 // returns persisting lines to normal and restores the limit this problem raised (if no
