@@ -107,9 +107,10 @@ typedef struct {
                              name: a strong F neighbour k of i adds its strong C points to
                              i's interpolatory set only when k shares no strong C point
                              with i; 0: extended+i [0] */
-    int l2_persist;       /* 1: with the FP64 preconditioner and the SGS smoother, keep the
-                             fine smoother's vector (8 n_h bytes) in the L2 persisting
-                             set-aside during its colour phases: an access-policy window
+    int l2_persist;       /* 1: with the FP64 preconditioner and the SGS smoother (additive
+                             or multiplicative form), keep the fine smoother's vector
+                             (8 n_h bytes) in the L2 persisting set-aside during its
+                             colour phases: an access-policy window
                              (persisting hits, streaming misses) on every phase launch.
                              Applied when that vector is at least a quarter of L2 and
                              1.125x it fits the largest set-aside; setup then raises the

@@ -120,6 +120,28 @@ void launch_pdl(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args... a
     launch_pdl_w(kern, grid, s, (const cudaAccessPolicyWindow *)nullptr, args...);
 }
 
+// a plain launch (no programmatic serialization) with an optional access-policy window
+template <typename... KArgs, typename... Args>
+void launch_w(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, const cudaAccessPolicyWindow *win,
+              Args... args) {
+    if (!win) {
+        kern<<<grid, kBlock, 0, s>>>(args...);
+        PK_LAUNCH();
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow = *win;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PK_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+    PK_LAUNCH();
+}
+
 // Lanes per row for a colour phase whose longest row part has `len` entries: the fewest
 // lanes (a power of two, at most 32) for which one batch of loads per lane covers the row.
 // A colour phase is latency-bound, and every extra batch is one more DRAM round trip.
@@ -252,16 +274,19 @@ void gs_backward0(const DSplit &sp, int tpr_fixed, PT *y, cudaStream_t s,
 
 // full backward GS sweep on A x = b from the current x
 template <typename PT>
-void gs_backward_full(const DSplit &sp, int tpr_fixed, const PT *b, PT *x, cudaStream_t s) {
+void gs_backward_full(const DSplit &sp, int tpr_fixed, const PT *b, PT *x, cudaStream_t s,
+                      const cudaAccessPolicyWindow *win = nullptr) {
     for (int c = sp.ncol - 1; c >= 0; --c) {
         int64_t pb = sp.off[c], pe = sp.off[c + 1];
         if (pe <= pb) continue;
         const int tpr = tpr_fixed > 0 ? tpr_fixed : lanes_for(std::max(sp.lmax[c], sp.umax[c]));
         const int nb = batch_for(tpr, std::max(sp.l90[c], sp.u90[c]));
-        PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (k_gs_bwd_full<TPR, NB, PT><<<rows_grid(pe - pb, TPR), kBlock, 0, s>>>(
-                                pb, pe, sp.perm, sp.lptr, sp.lcol, pick<PT>(sp.lval, sp.lval32), sp.uptr,
-                                sp.ucol, pick<PT>(sp.uval, sp.uval32), pick<PT>(sp.diag, sp.diag32), b, x))));
-        PK_LAUNCH();
+        PK_TPR_SWITCH(tpr, PK_NB_SWITCH(nb, (launch_w(k_gs_bwd_full<TPR, NB, PT>, rows_grid(pe - pb, TPR), s, win,
+                                                      pb, pe, (const int32_t *)sp.perm, (const int64_t *)sp.lptr,
+                                                      (const int32_t *)sp.lcol, pick<PT>(sp.lval, sp.lval32),
+                                                      (const int64_t *)sp.uptr, (const int32_t *)sp.ucol,
+                                                      pick<PT>(sp.uval, sp.uval32), pick<PT>(sp.diag, sp.diag32),
+                                                      b, x))));
     }
 }
 
@@ -398,6 +423,20 @@ void barrier_status(pkasp_problem *p, cudaStream_t s) {
     }
 }
 
+// the access-policy window that keeps the FP64 fine smoother's vector y in the L2
+// set-aside (l2_window_setup); nullptr when there is none
+template <typename PT>
+const cudaAccessPolicyWindow *smoother_window(const pkasp_problem *p, PT *y, cudaAccessPolicyWindow &win) {
+    if (!std::is_same<PT, double>::value || p->l2_win_bytes == 0) return nullptr;
+    win = cudaAccessPolicyWindow{};
+    win.base_ptr = (void *)y;
+    win.num_bytes = p->l2_win_bytes;
+    win.hitRatio = 1.0f;
+    win.hitProp = cudaAccessPropertyPersisting;
+    win.missProp = cudaAccessPropertyStreaming;
+    return &win;
+}
+
 // S_k r from zero into zs (PT)
 template <typename PT>
 void smoother(pkasp_problem *p, const double *r, PT *zs, cudaStream_t s) {
@@ -438,18 +477,10 @@ void smoother(pkasp_problem *p, const double *r, PT *zs, cudaStream_t s) {
         }
         return;
     }
-    // FP64: the access-policy window that keeps zs in the L2 set-aside (l2_window_setup)
-    cudaAccessPolicyWindow win = {};
-    const bool use_win = std::is_same<PT, double>::value && p->l2_win_bytes > 0;
-    if (use_win) {
-        win.base_ptr = (void *)zs;
-        win.num_bytes = p->l2_win_bytes;
-        win.hitRatio = 1.0f;
-        win.hitProp = cudaAccessPropertyPersisting;
-        win.missProp = cudaAccessPropertyStreaming;
-    }
-    gs_forward0<PT, double>(p->fine, ts, r, zs, s, use_win ? &win : nullptr);
-    gs_backward0<PT>(p->fine, ts, zs, s, use_win ? &win : nullptr);
+    cudaAccessPolicyWindow wb;
+    const cudaAccessPolicyWindow *win = smoother_window<PT>(p, zs, wb);
+    gs_forward0<PT, double>(p->fine, ts, r, zs, s, win);
+    gs_backward0<PT>(p->fine, ts, zs, s, win);
 }
 
 template <typename PT>
@@ -502,7 +533,8 @@ void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s, 
         k_jacobi0<PT, double><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, pick<PT>(p->d_l1h, p->d_l1h32), r, zs);
         PK_LAUNCH();
     } else {
-        gs_forward0<PT, double>(p->fine, tfw, r, zs, s);
+        cudaAccessPolicyWindow wb;
+        gs_forward0<PT, double>(p->fine, tfw, r, zs, s, smoother_window<PT>(p, zs, wb));
     }
     to_pt<PT>(r, rr, p->nh, s);
     PK_TPR_SWITCH(ta, (k_residual<TPR, PT, PT, PT><<<rows_grid(p->nh, TPR), kBlock, 0, s>>>(
@@ -521,7 +553,8 @@ void precondition(pkasp_problem *p, const double *r, double *z, cudaStream_t s, 
         k_add_div<PT><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, t, pick<PT>(p->d_l1h, p->d_l1h32), zs);
         PK_LAUNCH();
     } else {
-        gs_backward_full<PT>(p->fine, ts, (const PT *)rr, zs, s);
+        cudaAccessPolicyWindow wb;
+        gs_backward_full<PT>(p->fine, ts, (const PT *)rr, zs, s, smoother_window<PT>(p, zs, wb));
     }
     k_copy_to<PT><<<elem_grid(p->nh), kBlock, 0, s>>>(p->nh, zs, z);
     PK_LAUNCH();
@@ -884,7 +917,7 @@ void l2_window_setup(pkasp_problem *p) {
     p->l2_win_bytes = 0;
     const pkasp_options &o = p->opt;
     if (!o.l2_persist || o.precond_precision != PKASP_PREC_FP64 || o.smoother != PKASP_SMOOTHER_SGS ||
-        o.mode != PKASP_MODE_ADDITIVE) {
+        o.mode == PKASP_MODE_AMG) {
         l2_window_release(p);  // give back a set-aside an earlier setup of this problem took
         return;
     }
