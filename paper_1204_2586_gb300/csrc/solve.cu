@@ -921,21 +921,35 @@ void l2_window_setup(pkasp_problem *p) {
         l2_window_release(p);  // give back a set-aside an earlier setup of this problem took
         return;
     }
+    // best effort: where the device or the context refuses (no persisting L2, a limit it
+    // will not raise), the smoother simply runs without the window
     int dev = 0, l2 = 0, maxp = 0;
-    PK_CUDA(cudaGetDevice(&dev));
-    PK_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
-    PK_CUDA(cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev));
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
     const size_t y = sizeof(double) * (size_t)p->nh;
     const size_t mb = size_t(1) << 20;
     const size_t want = (y + y / 8 + mb - 1) / mb * mb;
     if (maxp <= 0 || y < (size_t)l2 / 4 || want > (size_t)maxp) return;
     size_t cur = 0;
-    PK_CUDA(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
     if (cur < want) {
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        size_t got = 0;
+        cudaDeviceGetLimit(&got, cudaLimitPersistingL2CacheSize);
+        cudaGetLastError();
         if (!p->l2_raised) p->l2_prev_limit = cur;
-        PK_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
-        PK_CUDA(cudaDeviceGetLimit(&p->l2_set_limit, cudaLimitPersistingL2CacheSize));
+        p->l2_set_limit = got;
         p->l2_raised = true;
+        if (got < y) return;  // granted less than the vector: no window
     }
     p->l2_win_bytes = y;
 }
